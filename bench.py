@@ -1,0 +1,367 @@
+"""Benchmark: Heisenberg-picture kicked-Ising propagation on the 127-qubit
+heavy-hex lattice through liborqa, reported as Pauli string-gate updates/s.
+
+One step = one full evolution of sigma_z^62 through T Trotter steps (the ZZ
+layer, the X layer with merge + truncation after every gate, and <M_t>
+after each step), starting from the operator resident in HBM.  The update
+count of a layer is the sum over its gates of |O| before the gate (144 ZZ
+gates + 127 X gates per step), the convention behind the paper's per-gate
+wall time (layer time / 271 gates).
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Under torchrun each rank runs its own replica of the workload on its own
+GPU (replicas only: the single-observable path is not sharded), the
+timings are max-reduced and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_13241_gb300 import workloads as W  # noqa: E402
+
+DEFAULT_WORKLOAD = "heavyhex"
+METRIC = "Pauli string-gate updates/s"
+UNIT = "string-gate updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="orqa", choices=["orqa", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--capacity", type=float, default=0.0, help="string capacity (0: from workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args(argv)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def default_capacity(wl):
+    # strings per buffer; the workspace is ~230 B per unit of capacity at W=2
+    return {"heavyhex": 1 << 21}.get(wl["name"], int(4e8))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def make_gpu_runner(wl, capacity, profile=True):
+    import numpy as np
+    import torch
+    from paper_2506_13241_gb300 import orqa as B
+
+    n = wl["n"]
+    ctx = B.Context(n, capacity, profile=profile)
+    layers = [B.gate_array(layer) for layer in wl["layers"]]
+    x_h, z_h = B.strings_from_labels([lab for lab, _ in wl["observable"]], n)
+    c_h = np.array([c for _, c in wl["observable"]], dtype=np.float64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x_d = torch.from_numpy(x_h.view(np.int64)).to(dev)
+    z_d = torch.from_numpy(z_h.view(np.int64)).to(dev)
+    c_d = torch.from_numpy(c_h).to(dev)
+    # pinned host copies for the end-to-end arm
+    x_p = torch.from_numpy(x_h.view(np.int64)).pin_memory()
+    z_p = torch.from_numpy(z_h.view(np.int64)).pin_memory()
+    c_p = torch.from_numpy(c_h).pin_memory()
+    delta = wl["delta"]
+
+    def evolve():
+        updates, mags, peak = 0, [], 0
+        for _ in range(wl["steps"]):
+            for layer in layers:
+                B.orqa_apply_layer(ctx.ctx, layer, delta)
+                s = B.orqa_stats(ctx.ctx)
+                updates += s["string_gate_updates"]
+                peak = max(peak, s["last_layer_peak"])
+            mags.append(B.orqa_expect(ctx.ctx))
+        return updates, mags, peak
+
+    def step_device():
+        ctx.set_operator_device(x_d, z_d, c_d)
+        return evolve()
+
+    def step_host():
+        B.orqa_set_operator(ctx.ctx, x_p.numpy().view(np.uint64), z_p.numpy().view(np.uint64),
+                            c_p.numpy())
+        return evolve()
+
+    h2d = x_h.nbytes + z_h.nbytes + c_h.nbytes
+    d2h = 8 * wl["steps"]
+    return ctx, step_device, step_host, h2d, d2h
+
+
+def run_gpu(args, wl, rank, world):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    capacity = int(args.capacity) if args.capacity else default_capacity(wl)
+    ctx, step_dev, step_host, h2d, d2h = make_gpu_runner(wl, capacity)
+    stream = ctx.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step_dev()
+    torch.cuda.synchronize()
+    ctx.profile_reset()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, total_updates, mags, peak = 0.0, 0, None, 0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            upd, mags, pk = step_dev()
+            e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_updates += upd
+        peak = max(peak, pk)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = ctx.profile()
+    # end to end through the public API with host buffers
+    e2e_s, e2e_updates = 0.0, 0
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        upd, _, _ = step_host()
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        e2e_updates += upd
+    times = [total_ms, e2e_s]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor(times, dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times = t.tolist()
+    return dict(total_ms=times[0], updates=total_updates, mags=mags, peak=peak, clocks=clk,
+                prof=prof, e2e_s=times[1], e2e_updates=e2e_updates, h2d=h2d, d2h=d2h,
+                capacity=capacity)
+
+
+def roofline_entry(prof, steps):
+    peak_gbs, peak_src = measured_peaks()
+    timed = [p for p in prof if p["launches"] > 0 and p["ms"] > 0]
+    if not timed:
+        return None
+    dom = max(timed, key=lambda p: p["ms"])
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+            "peak": peak_gbs, "peak_source": peak_src, "unit": "GB/s",
+            "frac": round(achieved / peak_gbs, 4), "traffic": None,
+            "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"],
+            "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+            "share_of_kernel_time": round(dom["ms"] / sum(p["ms"] for p in timed), 4),
+            "kernels": {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                                    "GB/s": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)}
+                        for p in timed}}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, seconds: float):
+    """Runs the oracle on the workload's first time steps, gate by gate,
+    until about ``seconds`` have passed; returns updates, time, steps."""
+    import oracle
+    n = wl["n"]
+    op = oracle.Oracle(n)
+    for lab, c in wl["observable"]:
+        op.add_label(lab, c)
+    updates, t_used, steps = 0, 0.0, 0
+    for t in range(wl["steps"]):
+        t0 = time.perf_counter()
+        for layer in wl["layers"]:
+            for g in layer:
+                updates += len(op)
+                op.apply(g, wl["delta"])
+        op.expect_zero()
+        t_used += time.perf_counter() - t0
+        steps = t + 1
+        if t_used >= seconds:
+            break
+    return updates, t_used, steps
+
+
+def cpu_baseline(wl, seconds):
+    upd, secs, steps = oracle_sample(wl, seconds)
+    return {"value": upd / secs if secs > 0 else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d time steps of %s (%d string-gate updates, %.1f s)" % (
+                steps, wl["steps"], wl["name"], upd, secs)}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    seconds = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(wl, seconds)
+    upd, secs, steps = 0, 0.0, 0
+    for _ in range(args.steps):
+        u, s, st = oracle_sample(wl, seconds)
+        upd += u
+        secs += s
+        steps = st
+    value = upd / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "first %d of %d time steps of %s per step" % (
+                                 steps, wl["steps"], wl["name"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(wl):
+    return {"workload": wl["name"], "lattice": "heavy-hex 127" if wl["n"] == 127 else "chain %d" % wl["n"],
+            "n_qubits": wl["n"], "theta_x": wl["theta_x"], "theta_zz": W.THETA_ZZ,
+            "observable": "Z_62" if wl["n"] == 127 else "Z_6", "time_steps": wl["steps"],
+            "delta": wl["delta"], "truncation": "absolute |c| < delta after every X gate",
+            "coefficients": "fp64", "l2": "flushed between timed steps"}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    wl = W.workload(args.workload)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    from paper_2506_13241_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    res = run_gpu(args, wl, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    total_updates = res["updates"] * world
+    secs = res["total_ms"] * 1e-3
+    value = total_updates / secs
+    e2e_value = res["e2e_updates"] * world / res["e2e_s"]
+    launches = sum(p["launches"] for p in res["prof"]) + sum(
+        p["launches"] for p in res["prof"] if p["name"] == "expect")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl),
+            "roofline": roofline_entry(res["prof"], args.steps),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
+                    "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": launches, "clocks": res["clocks"],
+            "magnetization": res["mags"], "peak_strings": res["peak"], "capacity": res["capacity"]}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

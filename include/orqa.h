@@ -1,0 +1,179 @@
+/*
+ * orqa.h -- C ABI of the GB300 sparse Pauli dynamics library (liborqa.so).
+ *
+ * The library propagates a real Pauli sum O = sum_I O_I sigma_I (Eq. define_O
+ * of arXiv 2506.13241) through rotation gates exp(-i theta/2 sigma_J) in the
+ * Heisenberg picture (Eq. update_rule), merging duplicate strings and
+ * truncating small coefficients after every non-Clifford gate (Algorithm 1),
+ * and evaluates <0|O|0> (Eq. magnetization).  Every step runs in CUDA kernels
+ * on the caller's stream; the host code only orchestrates.
+ *
+ * Pauli strings.  A string on n <= 128 qubits is a pair of bit planes
+ * (x, z) of W = (n <= 64 ? 1 : 2) little-endian uint64 words each; bit q of
+ * word q/64 belongs to qubit q.  (x_q, z_q) = (0,0) identity, (1,0) sigma_x,
+ * (1,1) sigma_y, (0,1) sigma_z.  This is a linear re-coding of the paper's
+ * two-bit local index (Sec. II: 00 = id, 01 = x, 10 = y, 11 = z):
+ * z = high bit, x = high xor low; it keeps the XOR product of Eq. orqaproduct.
+ * Host arrays of strings are string-major: word w of string i is at
+ * x[i * W + w].
+ *
+ * Memory.  The library allocates no device memory.  The caller passes one
+ * device buffer of at least orqa_workspace_bytes(n_qubits, capacity) bytes
+ * (for example a torch uint8 tensor) and keeps it alive until orqa_destroy.
+ * Host-side bookkeeping (the context) is allocated with malloc.
+ *
+ * Errors.  Every call returns an orqa_status; on failure the context keeps a
+ * message (orqa_last_error) and the operator held before the call is left
+ * unchanged (all layer work goes to scratch buffers that are committed only
+ * on success).
+ *
+ * Synchronisation.  Calls enqueue work on the context's stream.  Calls that
+ * return a host value (a live count, an expectation value, an export) wait
+ * for the stream.
+ */
+#ifndef ORQA_H
+#define ORQA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ORQA_OK = 0,
+    ORQA_EINVAL = 1,     /* bad argument: null pointer, size, qubit index, gate kind */
+    ORQA_ENOMEM = 2,     /* workspace smaller than orqa_workspace_bytes() */
+    ORQA_ECAPACITY = 3,  /* a result would exceed the capacity; operator unchanged */
+    ORQA_ECUDA = 4,      /* a CUDA runtime call failed (message holds its text) */
+    ORQA_ETIMEOUT = 5,   /* a bounded device-side wait ran out; operator unchanged */
+    ORQA_ESTATE = 6      /* call not valid in the current state */
+} orqa_status;
+
+/* Gate kinds.  Each gate is exp(-i theta/2 sigma_J) (App. A).
+ *   ORQA_RX : sigma_J = sigma_x on qubit q0 (any theta).
+ *   ORQA_RZZ: sigma_J = sigma_z on q0 times sigma_z on q1 (q0 != q1); theta
+ *             must be a multiple of pi/2 (Clifford), the only case of the
+ *             kicked Ising circuit (theta_zz = -pi/2, Eq. eq:u).
+ * An angle within 1e-12 of a multiple of pi/2 is applied as an exact
+ * Clifford rotation: (cos, sin) in {0, +1, -1}. */
+enum { ORQA_RX = 1, ORQA_RZZ = 2 };
+
+typedef struct {
+    int32_t kind;   /* ORQA_RX or ORQA_RZZ */
+    int32_t q0;     /* qubit (0-based) */
+    int32_t q1;     /* second qubit of ORQA_RZZ, ignored otherwise */
+    int32_t pad;    /* must be 0 */
+    double theta;   /* rotation angle */
+} orqa_gate;
+
+/* orqa_config.flags */
+enum {
+    ORQA_FLAG_PROFILE = 1    /* time every kernel launch with CUDA events on the
+                                context's stream (see orqa_profile) */
+};
+
+typedef struct {
+    int32_t n_qubits;        /* 1..128 */
+    int32_t flags;           /* 0 or ORQA_FLAG_PROFILE */
+    int64_t capacity;        /* most strings any intermediate set may hold */
+    void* workspace;         /* device buffer, 256-byte aligned */
+    uint64_t workspace_bytes;
+    void* stream;            /* cudaStream_t, or NULL for the default stream */
+} orqa_config;
+
+typedef struct {
+    int64_t n_strings;        /* |O|: live strings */
+    int64_t last_layer_in;    /* strings entering the last apply_layer */
+    int64_t last_layer_peak;  /* largest intermediate set inside it */
+    int64_t string_gate_updates; /* sum over its gates of |O| before the gate */
+    int64_t branch_events;    /* anticommuting (string, gate) pairs in it */
+    int64_t dropped;          /* strings removed by truncation in it */
+    int32_t chunk_passes;     /* device passes its rotation layer took */
+    int32_t pad;
+} orqa_stats_t;
+
+/* Per-kernel launch profile (ORQA_FLAG_PROFILE).  bytes is the kernel's
+ * algorithmic DRAM traffic: the bytes its inputs and outputs must move at
+ * least once (not counting hash-probe misses or cache effects). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double ms;               /* summed CUDA-event durations */
+    double bytes;            /* summed algorithmic bytes */
+} orqa_kernel_profile;
+
+typedef struct orqa_ctx orqa_ctx;
+
+/* Bytes of device workspace needed for n_qubits and capacity. */
+uint64_t orqa_workspace_bytes(int32_t n_qubits, int64_t capacity);
+
+/* Creates a context holding the empty operator.  The workspace and the
+ * stream stay owned by the caller.  EINVAL on bad sizes, ENOMEM if the
+ * workspace is too small. */
+orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out);
+
+/* Replaces the operator by the n strings in the HOST arrays x, z (n*W words
+ * each) and c (n doubles); the arrays are copied.  Duplicate strings are
+ * summed and exact zeros dropped (the insert-or-add of Algorithm 1).
+ * ECAPACITY if n > capacity. */
+orqa_status orqa_set_operator(orqa_ctx* ctx, int64_t n, const uint64_t* x,
+                              const uint64_t* z, const double* c);
+
+/* As orqa_set_operator, but x, z, c are DEVICE arrays in the same
+ * string-major layout, read on the context's stream. */
+orqa_status orqa_set_operator_device(orqa_ctx* ctx, int64_t n, const uint64_t* x,
+                                     const uint64_t* z, const double* c);
+
+/* Applies n_gates mutually commuting gates in array order (Eq. update_rule,
+ * one gate at a time as in Algorithm 1).  All gates must be of one kind.
+ *   ORQA_RZZ (Clifford): each string maps to exactly one string with an
+ *     exact sign; nothing merges and |c| is unchanged.  Strings with
+ *     |c| < delta are then dropped.
+ *   ORQA_RX: after every gate, duplicates are merged and strings with
+ *     c == 0 or |c| < delta are dropped (the truncation loop of Algorithm 1
+ *     with the absolute threshold); the result is the one of that per-gate
+ *     schedule, bit for bit.
+ * n_live_out (may be NULL) receives |O| after the layer.  ECAPACITY if an
+ * intermediate set would exceed the capacity (operator unchanged). */
+orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates,
+                             double delta, int64_t* n_live_out);
+
+/* Merges duplicate strings (sums their coefficients) and drops c == 0 and
+ * |c| < delta: the insert-or-add and truncate loops of Algorithm 1 applied
+ * to the whole operator.  n_live_out (may be NULL) receives |O|. */
+orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out);
+
+/* <0|O|0> = sum of O_I over strings with no sigma_x / sigma_y factor
+ * (x plane all zero), in FP64 (Eq. magnetization). */
+orqa_status orqa_expect(orqa_ctx* ctx, double* out);
+
+/* Copies the operator to HOST arrays (cap strings at most; x, z: cap*W
+ * words, c: cap doubles) in an unspecified order; *n_out receives |O|.
+ * ECAPACITY (nothing copied) if |O| > cap. */
+orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c,
+                        int64_t* n_out);
+
+/* Counters of the operator and of the last apply_layer call. */
+orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out);
+
+/* Profile of kernel kind `index` (0 <= index < orqa_profile_count()) since
+ * the last reset; zeros unless the context was created with
+ * ORQA_FLAG_PROFILE.  EINVAL for an index out of range. */
+int32_t orqa_profile_count(void);
+orqa_status orqa_profile(orqa_ctx* ctx, int32_t index, orqa_kernel_profile* out);
+orqa_status orqa_profile_reset(orqa_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next
+ * call on ctx. */
+const char* orqa_last_error(const orqa_ctx* ctx);
+
+/* Releases the host context (the caller's workspace is not freed). */
+void orqa_destroy(orqa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORQA_H */

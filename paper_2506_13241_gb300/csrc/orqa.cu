@@ -1,0 +1,668 @@
+// liborqa: C ABI (include/orqa.h) and host orchestration of the kernels in
+// orqa_kernels.cuh.  The host side validates arguments, carves the caller's
+// workspace, computes cos/sin of each gate once, launches kernels on the
+// caller's stream and reads back small counters; every per-string step runs
+// on the device.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "orqa.h"
+#include "orqa_kernels.cuh"
+
+using namespace orqa;
+
+namespace {
+enum KernelKind {
+    K_RZZ, K_TRUNCATE, K_SPLIT, K_ASSIGN, K_OFFSETS, K_SCATTER, K_PROCESS,
+    K_MERGE_ASSIGN, K_MERGE_REDUCE, K_EXPECT, K_COUNT
+};
+const char* const KERNEL_NAMES[K_COUNT] = {
+    "rzz_layer", "truncate", "rx_split", "unit_assign", "unit_offsets", "unit_scatter",
+    "unit_process", "merge_assign", "merge_reduce", "expect"};
+
+struct PendingLaunch {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+};
+}  // namespace
+
+struct orqa_ctx {
+    int n_qubits = 0;
+    int W = 1;
+    long long cap = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 1;
+
+    StrList buf[4];
+    int cur = 0;            // buffer holding the operator
+    long long n = 0;        // |O|
+    double clean_delta = 0; // no live coefficient is below this
+
+    int32_t* uid = nullptr;
+    int32_t* rank = nullptr;
+    uint8_t* idx = nullptr;
+    uint64_t* unit_z = nullptr;
+    uint64_t* unit_xb = nullptr;
+    int32_t* unit_count = nullptr;
+    long long* unit_off = nullptr;
+    double* sorted_c = nullptr;
+    uint8_t* sorted_idx = nullptr;
+    int32_t* table = nullptr;
+    long long table_cap = 0;
+    Counters* ctr = nullptr;
+    unsigned long long* pop_delta = nullptr;
+    double* partials = nullptr;
+    double* scalar = nullptr;
+
+    orqa_stats_t stats{};
+    std::string err;
+
+    // ORQA_FLAG_PROFILE: CUDA events around every launch, resolved at the
+    // next stream synchronisation.
+    bool profile = false;
+    std::vector<PendingLaunch> pending;
+    std::vector<cudaEvent_t> event_pool;
+    long long prof_launches[K_COUNT] = {};
+    double prof_ms[K_COUNT] = {};
+    double prof_bytes[K_COUNT] = {};
+
+    ~orqa_ctx() {
+        for (auto& p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : event_pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+long long pow2_at_least(long long v) {
+    long long p = 1024;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct Layout {
+    size_t str_x, str_c;  // per string buffer: x and z planes, c
+    size_t total;
+    long long table_cap;
+};
+
+// Offsets are computed in the same order by workspace_bytes and carve().
+Layout layout(int n_qubits, long long cap) {
+    Layout L{};
+    const int W = n_qubits <= 64 ? 1 : 2;
+    const size_t C = (size_t)cap;
+    L.str_x = align_up(C * W * 8);
+    L.str_c = align_up(C * 8);
+    L.table_cap = pow2_at_least(2 * cap);
+    size_t t = 0;
+    t += 4 * (2 * L.str_x + L.str_c);     // four string buffers
+    t += 2 * align_up(C * 4);              // uid, rank
+    t += align_up(C);                      // idx
+    t += 2 * L.str_x;                      // unit_z, unit_xb
+    t += align_up(C * 4);                  // unit_count
+    t += align_up(C * 8);                  // unit_off
+    t += align_up(C * 8);                  // sorted_c
+    t += align_up(C);                      // sorted_idx
+    t += align_up((size_t)L.table_cap * 4);  // hash table
+    t += align_up(sizeof(Counters));
+    t += align_up(MAX_QUBITS * 8);
+    t += align_up(EXPECT_BLOCKS * 8);
+    t += align_up(64);
+    L.total = t;
+    return L;
+}
+
+orqa_status fail(orqa_ctx* ctx, orqa_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+#define CUDA_TRY(ctx, expr)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, ORQA_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LAUNCH_CHECK(ctx)                                                               \
+    do {                                                                                \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, ORQA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// cos and sin of a rotation angle, exact (0, +-1) within 1e-12 of a
+// multiple of pi/2.
+void cos_sin(double theta, double* c, double* s, bool* clifford) {
+    const double half_pi = 1.57079632679489661923;
+    const double k = std::nearbyint(theta / half_pi);
+    if (std::fabs(theta - k * half_pi) <= 1e-12) {
+        const long long m = (((long long)k % 4) + 4) % 4;
+        static const double tab[4][2] = {{1.0, 0.0}, {0.0, 1.0}, {-1.0, 0.0}, {0.0, -1.0}};
+        *c = tab[m][0];
+        *s = tab[m][1];
+        *clifford = true;
+        return;
+    }
+    *c = std::cos(theta);
+    *s = std::sin(theta);
+    *clifford = false;
+}
+
+int grid_for(const orqa_ctx* ctx, long long n, int block = 256, int per_sm = 8) {
+    long long b = (n + block - 1) / block;
+    long long cap = (long long)ctx->sm_count * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaEvent_t take_event(orqa_ctx* ctx) {
+    cudaEvent_t e = nullptr;
+    if (!ctx->event_pool.empty()) {
+        e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    return e;
+}
+
+// Returns the index of the pending record (or -1) so that the byte count can
+// be filled in once the counters are known.
+int prof_begin(orqa_ctx* ctx, int kind, double bytes) {
+    if (!ctx->profile) return -1;
+    PendingLaunch p{kind, take_event(ctx), take_event(ctx), bytes};
+    cudaEventRecord(p.a, ctx->stream);
+    ctx->pending.push_back(p);
+    return (int)ctx->pending.size() - 1;
+}
+
+void prof_end(orqa_ctx* ctx, int rec) {
+    if (rec >= 0) cudaEventRecord(ctx->pending[rec].b, ctx->stream);
+}
+
+void prof_set_bytes(orqa_ctx* ctx, int rec, double bytes) {
+    if (rec >= 0) ctx->pending[rec].bytes = bytes;
+}
+
+// Call only after the stream has been synchronised.
+void prof_resolve(orqa_ctx* ctx) {
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->prof_ms[p.kind] += ms;
+            ctx->prof_bytes[p.kind] += p.bytes;
+            ctx->prof_launches[p.kind] += 1;
+        }
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
+
+orqa_status sync_counters(orqa_ctx* ctx, Counters* h) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(h, ctx->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return ORQA_OK;
+}
+
+orqa_status reset_counters(orqa_ctx* ctx) {
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->stream));
+    return ORQA_OK;
+}
+
+orqa_status check_flags(orqa_ctx* ctx, const Counters& h, const char* what) {
+    if (h.timeout)
+        return fail(ctx, ORQA_ETIMEOUT, std::string(what) + ": a bounded hash-table wait ran out");
+    if (h.table_full) return fail(ctx, ORQA_ECAPACITY, std::string(what) + ": hash table full");
+    if (h.overflow) {
+        char b[256];
+        snprintf(b, sizeof b, "%s: result exceeds capacity %lld (needed at least %llu + %llu)", what,
+                 ctx->cap, (unsigned long long)h.n_done, (unsigned long long)h.n_next);
+        return fail(ctx, ORQA_ECAPACITY, b);
+    }
+    return ORQA_OK;
+}
+
+template <int W>
+orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, double delta,
+                       long long* n_out) {
+    RxRun run{};  // unused in full-key mode
+    const long long tcap = pow2_at_least(2 * (n > 0 ? n : 1));
+    if (tcap > ctx->table_cap) return fail(ctx, ORQA_ECAPACITY, "merge: hash table too small");
+    if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+    int r_as = -1, r_off = -1, r_sc = -1, r_red = -1;
+    if (n > 0) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->table, 0xff, (size_t)tcap * 4, ctx->stream));
+        const int g = grid_for(ctx, n);
+        r_as = prof_begin(ctx, K_MERGE_ASSIGN, 0);
+        k_unit_assign<W, true><<<g, 256, 0, ctx->stream>>>(src, n, run, 0, ctx->table, tcap - 1,
+                                                           ctx->unit_z, ctx->unit_xb, ctx->unit_count,
+                                                           ctx->uid, ctx->rank, ctx->idx, ctx->ctr);
+        prof_end(ctx, r_as);
+        LAUNCH_CHECK(ctx);
+        r_off = prof_begin(ctx, K_OFFSETS, 0);
+        k_unit_offsets<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(ctx->unit_count, ctx->unit_off, ctx->ctr);
+        prof_end(ctx, r_off);
+        LAUNCH_CHECK(ctx);
+        r_sc = prof_begin(ctx, K_SCATTER, 0);
+        k_unit_scatter<false><<<g, 256, 0, ctx->stream>>>(src.c, n, ctx->uid, ctx->rank, ctx->idx,
+                                                          ctx->unit_off, ctx->sorted_c, ctx->sorted_idx);
+        prof_end(ctx, r_sc);
+        LAUNCH_CHECK(ctx);
+        r_red = prof_begin(ctx, K_MERGE_REDUCE, 0);
+        k_merge_reduce<W><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(
+            ctx->unit_z, ctx->unit_xb, ctx->unit_count, ctx->unit_off, ctx->sorted_c, delta,
+            ctx->buf[dst_buf], ctx->cap, ctx->ctr);
+        prof_end(ctx, r_red);
+        LAUNCH_CHECK(ctx);
+    }
+    Counters h{};
+    orqa_status st = sync_counters(ctx, &h);
+    if (st != ORQA_OK) return st;
+    {
+        const double R = 8.0 * (2 * W + 1), nu = (double)h.n_units, nn = (double)n;
+        prof_set_bytes(ctx, r_as, nn * (32.0 * W + 13.0) + nu * (16.0 * W + 4.0));
+        prof_set_bytes(ctx, r_off, nu * 12.0);
+        prof_set_bytes(ctx, r_sc, nn * 32.0);
+        prof_set_bytes(ctx, r_red, nu * (16.0 * W + 12.0) + nn * 8.0 + (double)h.n_done * R);
+        prof_resolve(ctx);
+    }
+    st = check_flags(ctx, h, "merge");
+    if (st != ORQA_OK) return st;
+    *n_out = (long long)h.n_done;
+    ctx->stats.dropped = (int64_t)h.dropped;
+    return ORQA_OK;
+}
+
+template <int W>
+orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
+    std::vector<ZZLayer> launches;
+    ZZLayer L{};
+    for (int k = 0; k < ng; ++k) {
+        double c, s;
+        bool cl;
+        cos_sin(g[k].theta, &c, &s, &cl);
+        if (!cl) return fail(ctx, ORQA_EINVAL, "ORQA_RZZ angle must be a multiple of pi/2");
+        int mode;
+        if (s == 0.0)
+            mode = (c > 0) ? 0 : 1;
+        else
+            mode = (s < 0) ? 2 : 3;
+        if (mode == 0) continue;
+        if (L.n_edges == MAX_EDGES) {
+            launches.push_back(L);
+            L = ZZLayer{};
+        }
+        L.qi[L.n_edges] = (uint8_t)g[k].q0;
+        L.qj[L.n_edges] = (uint8_t)g[k].q1;
+        L.mode[L.n_edges] = (uint8_t)mode;
+        ++L.n_edges;
+    }
+    if (L.n_edges) launches.push_back(L);
+    StrList s = ctx->buf[ctx->cur];
+    for (const ZZLayer& l : launches) {
+        if (ctx->n == 0) break;
+        const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (8.0 * (2 * W + 1) + 8.0 * W + 8.0));
+        k_rzz_layer<W><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, l);
+        prof_end(ctx, r);
+        LAUNCH_CHECK(ctx);
+    }
+    ctx->stats.last_layer_in = ctx->n;
+    ctx->stats.last_layer_peak = ctx->n;
+    ctx->stats.string_gate_updates = (int64_t)ctx->n * ng;
+    ctx->stats.branch_events = 0;
+    ctx->stats.dropped = 0;
+    ctx->stats.chunk_passes = 0;
+    if (delta > ctx->clean_delta && ctx->n > 0) {
+        const int dst = (ctx->cur + 1) % 4;
+        if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+        const int r = prof_begin(ctx, K_TRUNCATE, 0);
+        k_truncate<W><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, ctx->buf[dst], ctx->cap,
+                                                                     delta, ctx->ctr);
+        prof_end(ctx, r);
+        LAUNCH_CHECK(ctx);
+        Counters h{};
+        orqa_status st = sync_counters(ctx, &h);
+        if (st != ORQA_OK) return st;
+        prof_set_bytes(ctx, r, (double)ctx->n * 8.0 + (double)h.n_done * (16.0 * W + 8.0 * (2 * W + 1)));
+        prof_resolve(ctx);
+        if ((st = check_flags(ctx, h, "truncate")) != ORQA_OK) return st;
+        ctx->stats.dropped = ctx->n - (long long)h.n_done;
+        ctx->n = (long long)h.n_done;
+        ctx->cur = dst;
+        ctx->clean_delta = delta;
+    }
+    return ORQA_OK;
+}
+
+template <int W>
+orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
+    RxRun run{};
+    run.delta = delta;
+    run.q_first = g[0].q0;
+    for (int k = 0; k < ng; ++k) {
+        const int q = g[k].q0;
+        if (k > 0 && q <= g[k - 1].q0)
+            return fail(ctx, ORQA_EINVAL, "ORQA_RX gates of one layer must have strictly ascending qubits");
+        run.mask[q >> 6] |= 1ull << (q & 63);
+        bool cl;
+        cos_sin(g[k].theta, &run.cs[q], &run.sn[q], &cl);
+    }
+    const int S = ctx->cur;
+    const int D = (S + 1) % 4, A0 = (S + 2) % 4, A1 = (S + 3) % 4;
+    const long long n_in = ctx->n;
+    if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
+    const double R = 8.0 * (2 * W + 1);
+    int r_split = -1;
+    if (n_in > 0) {
+        r_split = prof_begin(ctx, K_SPLIT, 0);
+        k_rx_split<W><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[S], n_in, ctx->buf[D],
+                                                                   ctx->buf[A0], ctx->cap, run, ctx->ctr);
+        prof_end(ctx, r_split);
+        LAUNCH_CHECK(ctx);
+    }
+    Counters h{};
+    orqa_status st = sync_counters(ctx, &h);
+    if (st != ORQA_OK) return st;
+    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + 8.0) + (double)(h.n_done + h.n_next) * (8.0 * W + R));
+    prof_resolve(ctx);
+    if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
+    const unsigned long long split_dropped = h.dropped;
+    long long n_active = (long long)h.n_next;
+    long long peak = (long long)h.n_done + n_active;
+    int a_cur = A0, a_next = A1;
+    int pass = 0;
+    const int g_units = ctx->sm_count * 8;
+    while (n_active > 0) {
+        const long long tcap = pow2_at_least(2 * n_active);
+        if (tcap > ctx->table_cap) return fail(ctx, ORQA_ECAPACITY, "rotation layer: hash table too small");
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->table, 0xff, (size_t)tcap * 4, ctx->stream));
+        // fresh unit bookkeeping and next-list cursor for this pass
+        CUDA_TRY(ctx, cudaMemsetAsync(&ctx->ctr->n_next, 0, 3 * sizeof(unsigned long long), ctx->stream));
+        const int g = grid_for(ctx, n_active);
+        const unsigned long long done_before = h.n_done;
+        const int r_as = prof_begin(ctx, K_ASSIGN, 0);
+        k_unit_assign<W, false><<<g, 256, 0, ctx->stream>>>(
+            ctx->buf[a_cur], n_active, run, pass, ctx->table, tcap - 1, ctx->unit_z, ctx->unit_xb,
+            ctx->unit_count, ctx->uid, ctx->rank, ctx->idx, ctx->ctr);
+        prof_end(ctx, r_as);
+        LAUNCH_CHECK(ctx);
+        const int r_off = prof_begin(ctx, K_OFFSETS, 0);
+        k_unit_offsets<<<g, 256, 0, ctx->stream>>>(ctx->unit_count, ctx->unit_off, ctx->ctr);
+        prof_end(ctx, r_off);
+        LAUNCH_CHECK(ctx);
+        const int r_sc = prof_begin(ctx, K_SCATTER, (double)n_active * 34.0);
+        k_unit_scatter<true><<<g, 256, 0, ctx->stream>>>(ctx->buf[a_cur].c, n_active, ctx->uid, ctx->rank,
+                                                         ctx->idx, ctx->unit_off, ctx->sorted_c,
+                                                         ctx->sorted_idx);
+        prof_end(ctx, r_sc);
+        LAUNCH_CHECK(ctx);
+        const int r_pr = prof_begin(ctx, K_PROCESS, 0);
+        k_unit_process<W><<<g_units, PROCESS_WARPS * 32, 0, ctx->stream>>>(
+            ctx->unit_z, ctx->unit_xb, ctx->unit_count, ctx->unit_off, ctx->sorted_c, ctx->sorted_idx,
+            run, pass, ctx->buf[D], ctx->buf[a_next], ctx->cap, ctx->ctr, ctx->pop_delta);
+        prof_end(ctx, r_pr);
+        LAUNCH_CHECK(ctx);
+        if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
+        {
+            const double nu = (double)h.n_units, na = (double)n_active;
+            const double outs = (double)(h.n_done - done_before) + (double)h.n_next;
+            prof_set_bytes(ctx, r_as, na * (32.0 * W + 13.0) + nu * (16.0 * W + 4.0));
+            prof_set_bytes(ctx, r_off, nu * 12.0);
+            prof_set_bytes(ctx, r_pr, nu * (16.0 * W + 12.0) + na * 9.0 + outs * R);
+            prof_resolve(ctx);
+        }
+        if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
+        n_active = (long long)h.n_next;
+        if ((long long)h.n_done + n_active > peak) peak = (long long)h.n_done + n_active;
+        const int t = a_cur;
+        a_cur = a_next;
+        a_next = t;
+        ++pass;
+    }
+    // Sum over the gates of |O| before each gate: |O| changes at gate q by
+    // the population delta recorded there (and by the strings the entry
+    // split dropped at the first gate).
+    std::vector<unsigned long long> pd(MAX_QUBITS);
+    CUDA_TRY(ctx, cudaMemcpyAsync(pd.data(), ctx->pop_delta, MAX_QUBITS * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    long long pop = n_in, updates = 0;
+    for (int k = 0; k < ng; ++k) {
+        updates += pop;
+        const int q = g[k].q0;
+        pop += (long long)pd[q];
+        if (k == 0) pop -= (long long)split_dropped;
+    }
+    ctx->cur = D;
+    ctx->n = (long long)h.n_done;
+    ctx->clean_delta = delta;
+    ctx->stats.last_layer_in = n_in;
+    ctx->stats.last_layer_peak = peak;
+    ctx->stats.string_gate_updates = updates;
+    ctx->stats.branch_events = (int64_t)h.branch_events;
+    ctx->stats.dropped = (int64_t)h.dropped;
+    ctx->stats.chunk_passes = pass;
+    return ORQA_OK;
+}
+
+template <int W>
+orqa_status expect_impl(orqa_ctx* ctx, double* out) {
+    const int nb = EXPECT_BLOCKS;
+    const int r = prof_begin(ctx, K_EXPECT, (double)ctx->n * (8.0 * W + 8.0));
+    k_expect_partial<W><<<nb, 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->partials);
+    k_expect_final<<<1, 32, 0, ctx->stream>>>(ctx->partials, nb, ctx->scalar);
+    prof_end(ctx, r);
+    LAUNCH_CHECK(ctx);
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->scalar, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_resolve(ctx);
+    return ORQA_OK;
+}
+
+orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z, const double* c,
+                     cudaMemcpyKind kind) {
+    if (!ctx) return ORQA_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !z || !c))) return fail(ctx, ORQA_EINVAL, "set_operator: bad arguments");
+    if (n > ctx->cap) return fail(ctx, ORQA_ECAPACITY, "set_operator: n exceeds capacity");
+    const int W = ctx->W;
+    const int stage = (ctx->cur + 1) % 4, dst = (ctx->cur + 2) % 4;
+    StrList s = ctx->buf[stage];
+    if (n > 0) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.x, x, (size_t)n * W * 8, kind, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.z, z, (size_t)n * W * 8, kind, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.c, c, (size_t)n * 8, kind, ctx->stream));
+    }
+    long long m = 0;
+    orqa_status st = (W == 1) ? merge_into<1>(ctx, s, n, dst, 0.0, &m) : merge_into<2>(ctx, s, n, dst, 0.0, &m);
+    if (st != ORQA_OK) return st;
+    ctx->cur = dst;
+    ctx->n = m;
+    ctx->clean_delta = 0.0;
+    ctx->stats = orqa_stats_t{};
+    ctx->err.clear();
+    return ORQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t orqa_workspace_bytes(int32_t n_qubits, int64_t capacity) {
+    if (n_qubits < 1 || n_qubits > 128 || capacity < 1 || capacity > 0x7fffffffLL) return 0;
+    return (uint64_t)layout(n_qubits, capacity).total;
+}
+
+orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
+    if (!cfg || !out) return ORQA_EINVAL;
+    *out = nullptr;
+    if (cfg->n_qubits < 1 || cfg->n_qubits > 128 || cfg->capacity < 1 || cfg->capacity > 0x7fffffffLL ||
+        (cfg->flags & ~ORQA_FLAG_PROFILE) != 0 || !cfg->workspace || ((uintptr_t)cfg->workspace % ALIGN) != 0)
+        return ORQA_EINVAL;
+    const Layout L = layout(cfg->n_qubits, cfg->capacity);
+    if (cfg->workspace_bytes < L.total) return ORQA_ENOMEM;
+    orqa_ctx* ctx = new orqa_ctx();
+    ctx->n_qubits = cfg->n_qubits;
+    ctx->W = cfg->n_qubits <= 64 ? 1 : 2;
+    ctx->cap = cfg->capacity;
+    ctx->stream = (cudaStream_t)cfg->stream;
+    ctx->profile = (cfg->flags & ORQA_FLAG_PROFILE) != 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete ctx;
+        return ORQA_ECUDA;
+    }
+    char* p = (char*)cfg->workspace;
+    const size_t C = (size_t)cfg->capacity;
+    for (int b = 0; b < 4; ++b) {
+        ctx->buf[b].x = (uint64_t*)p; p += L.str_x;
+        ctx->buf[b].z = (uint64_t*)p; p += L.str_x;
+        ctx->buf[b].c = (double*)p;   p += L.str_c;
+    }
+    ctx->uid = (int32_t*)p; p += align_up(C * 4);
+    ctx->rank = (int32_t*)p; p += align_up(C * 4);
+    ctx->idx = (uint8_t*)p; p += align_up(C);
+    ctx->unit_z = (uint64_t*)p; p += L.str_x;
+    ctx->unit_xb = (uint64_t*)p; p += L.str_x;
+    ctx->unit_count = (int32_t*)p; p += align_up(C * 4);
+    ctx->unit_off = (long long*)p; p += align_up(C * 8);
+    ctx->sorted_c = (double*)p; p += align_up(C * 8);
+    ctx->sorted_idx = (uint8_t*)p; p += align_up(C);
+    ctx->table = (int32_t*)p; p += align_up((size_t)L.table_cap * 4);
+    ctx->table_cap = L.table_cap;
+    ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));
+    ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
+    ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);
+    ctx->scalar = (double*)p; p += align_up(64);
+    *out = ctx;
+    return ORQA_OK;
+}
+
+orqa_status orqa_set_operator(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z,
+                              const double* c) {
+    return set_from(ctx, n, x, z, c, cudaMemcpyHostToDevice);
+}
+
+orqa_status orqa_set_operator_device(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z,
+                                     const double* c) {
+    return set_from(ctx, n, x, z, c, cudaMemcpyDeviceToDevice);
+}
+
+orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates, double delta,
+                             int64_t* n_live_out) {
+    if (!ctx) return ORQA_EINVAL;
+    if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(ctx, ORQA_EINVAL, "apply_layer: bad gate array");
+    if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "apply_layer: delta must be finite and >= 0");
+    if (n_gates == 0) {
+        if (n_live_out) *n_live_out = ctx->n;
+        return ORQA_OK;
+    }
+    const int kind = gates[0].kind;
+    for (int k = 0; k < n_gates; ++k) {
+        const orqa_gate& g = gates[k];
+        if (g.kind != kind) return fail(ctx, ORQA_EINVAL, "apply_layer: all gates of a layer must be of one kind");
+        if (g.pad != 0 || !std::isfinite(g.theta)) return fail(ctx, ORQA_EINVAL, "apply_layer: bad gate field");
+        if (g.q0 < 0 || g.q0 >= ctx->n_qubits) return fail(ctx, ORQA_EINVAL, "apply_layer: qubit out of range");
+        if (kind == ORQA_RZZ && (g.q1 < 0 || g.q1 >= ctx->n_qubits || g.q1 == g.q0))
+            return fail(ctx, ORQA_EINVAL, "apply_layer: bad second qubit");
+        if (kind != ORQA_RX && kind != ORQA_RZZ) return fail(ctx, ORQA_EINVAL, "apply_layer: unknown gate kind");
+    }
+    orqa_status st;
+    if (kind == ORQA_RZZ)
+        st = (ctx->W == 1) ? apply_rzz<1>(ctx, gates, n_gates, delta) : apply_rzz<2>(ctx, gates, n_gates, delta);
+    else
+        st = (ctx->W == 1) ? apply_rx<1>(ctx, gates, n_gates, delta) : apply_rx<2>(ctx, gates, n_gates, delta);
+    if (st != ORQA_OK) return st;
+    ctx->stats.n_strings = ctx->n;
+    if (n_live_out) *n_live_out = ctx->n;
+    ctx->err.clear();
+    return ORQA_OK;
+}
+
+orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out) {
+    if (!ctx) return ORQA_EINVAL;
+    if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "merge_truncate: bad delta");
+    const int dst = (ctx->cur + 1) % 4;
+    long long m = 0;
+    orqa_status st = (ctx->W == 1) ? merge_into<1>(ctx, ctx->buf[ctx->cur], ctx->n, dst, delta, &m)
+                                   : merge_into<2>(ctx, ctx->buf[ctx->cur], ctx->n, dst, delta, &m);
+    if (st != ORQA_OK) return st;
+    ctx->cur = dst;
+    ctx->n = m;
+    if (delta > ctx->clean_delta) ctx->clean_delta = delta;
+    ctx->stats.n_strings = m;
+    if (n_live_out) *n_live_out = m;
+    ctx->err.clear();
+    return ORQA_OK;
+}
+
+orqa_status orqa_expect(orqa_ctx* ctx, double* out) {
+    if (!ctx || !out) return ORQA_EINVAL;
+    return (ctx->W == 1) ? expect_impl<1>(ctx, out) : expect_impl<2>(ctx, out);
+}
+
+orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c, int64_t* n_out) {
+    if (!ctx || !n_out) return ORQA_EINVAL;
+    *n_out = ctx->n;
+    if (ctx->n > cap) return fail(ctx, ORQA_ECAPACITY, "export: operator larger than cap");
+    if (ctx->n > 0 && (!x || !z || !c)) return fail(ctx, ORQA_EINVAL, "export: null array");
+    const StrList s = ctx->buf[ctx->cur];
+    const size_t n = (size_t)ctx->n;
+    if (n > 0) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(x, s.x, n * ctx->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(z, s.z, n * ctx->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(c, s.c, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return ORQA_OK;
+}
+
+orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out) {
+    if (!ctx || !out) return ORQA_EINVAL;
+    ctx->stats.n_strings = ctx->n;
+    *out = ctx->stats;
+    return ORQA_OK;
+}
+
+int32_t orqa_profile_count(void) { return K_COUNT; }
+
+orqa_status orqa_profile(orqa_ctx* ctx, int32_t index, orqa_kernel_profile* out) {
+    if (!ctx || !out || index < 0 || index >= K_COUNT) return ORQA_EINVAL;
+    memset(out, 0, sizeof(*out));
+    strncpy(out->name, KERNEL_NAMES[index], sizeof(out->name) - 1);
+    out->launches = ctx->prof_launches[index];
+    out->ms = ctx->prof_ms[index];
+    out->bytes = ctx->prof_bytes[index];
+    return ORQA_OK;
+}
+
+orqa_status orqa_profile_reset(orqa_ctx* ctx) {
+    if (!ctx) return ORQA_EINVAL;
+    for (int k = 0; k < K_COUNT; ++k) {
+        ctx->prof_launches[k] = 0;
+        ctx->prof_ms[k] = 0.0;
+        ctx->prof_bytes[k] = 0.0;
+    }
+    return ORQA_OK;
+}
+
+const char* orqa_last_error(const orqa_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void orqa_destroy(orqa_ctx* ctx) { delete ctx; }
+
+}  // extern "C"

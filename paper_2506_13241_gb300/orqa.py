@@ -1,0 +1,303 @@
+"""Thin Python binding of liborqa (include/orqa.h).
+
+Each ``orqa_*`` function here has the name of the C entry point it calls and
+only marshals arguments: numpy host arrays and torch device tensors become
+pointers, workload gate tuples become ``orqa_gate`` records.  Every step of
+the sparse Pauli dynamics runs in the CUDA library.  PyTorch supplies the
+device workspace and the stream.  There is no CPU fallback: if the library
+or a CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ORQA_OK, ORQA_EINVAL, ORQA_ENOMEM, ORQA_ECAPACITY, ORQA_ECUDA, ORQA_ETIMEOUT, ORQA_ESTATE = range(7)
+STATUS_NAMES = ["ORQA_OK", "ORQA_EINVAL", "ORQA_ENOMEM", "ORQA_ECAPACITY", "ORQA_ECUDA",
+                "ORQA_ETIMEOUT", "ORQA_ESTATE"]
+ORQA_RX, ORQA_RZZ = 1, 2
+ORQA_FLAG_PROFILE = 1
+EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_set_operator_device",
+            "orqa_apply_layer", "orqa_merge_truncate", "orqa_expect", "orqa_export", "orqa_stats",
+            "orqa_profile_count", "orqa_profile", "orqa_profile_reset",
+            "orqa_last_error", "orqa_destroy"]
+
+
+class orqa_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("theta", ctypes.c_double)]
+
+
+class orqa_config(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("flags", ctypes.c_int32), ("capacity", ctypes.c_int64),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
+class orqa_stats_t(ctypes.Structure):
+    _fields_ = [("n_strings", ctypes.c_int64), ("last_layer_in", ctypes.c_int64),
+                ("last_layer_peak", ctypes.c_int64), ("string_gate_updates", ctypes.c_int64),
+                ("branch_events", ctypes.c_int64), ("dropped", ctypes.c_int64),
+                ("chunk_passes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class orqa_kernel_profile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+class OrqaError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, message))
+
+
+_lib = None
+
+
+def library(path: str | None = None) -> ctypes.CDLL:
+    """Loads liborqa.so (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        path = path or _build.LIB
+        if not os.path.exists(path):
+            raise OSError("liborqa.so not built: run paper_2506_13241_gb300.build.build() (%s)" % path)
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        dpp = ctypes.POINTER(ctypes.c_double)
+        lib.orqa_workspace_bytes.restype = ctypes.c_uint64
+        lib.orqa_workspace_bytes.argtypes = [i32, i64]
+        lib.orqa_create.restype = i32
+        lib.orqa_create.argtypes = [ctypes.POINTER(orqa_config), ctypes.POINTER(vp)]
+        for name in ("orqa_set_operator", "orqa_set_operator_device"):
+            f = getattr(lib, name)
+            f.restype = i32
+            f.argtypes = [vp, i64, vp, vp, vp]
+        lib.orqa_apply_layer.restype = i32
+        lib.orqa_apply_layer.argtypes = [vp, ctypes.POINTER(orqa_gate), i32, dp, ctypes.POINTER(i64)]
+        lib.orqa_merge_truncate.restype = i32
+        lib.orqa_merge_truncate.argtypes = [vp, dp, ctypes.POINTER(i64)]
+        lib.orqa_expect.restype = i32
+        lib.orqa_expect.argtypes = [vp, dpp]
+        lib.orqa_export.restype = i32
+        lib.orqa_export.argtypes = [vp, i64, u64p, u64p, dpp, ctypes.POINTER(i64)]
+        lib.orqa_stats.restype = i32
+        lib.orqa_stats.argtypes = [vp, ctypes.POINTER(orqa_stats_t)]
+        lib.orqa_profile_count.restype = i32
+        lib.orqa_profile_count.argtypes = []
+        lib.orqa_profile.restype = i32
+        lib.orqa_profile.argtypes = [vp, i32, ctypes.POINTER(orqa_kernel_profile)]
+        lib.orqa_profile_reset.restype = i32
+        lib.orqa_profile_reset.argtypes = [vp]
+        lib.orqa_last_error.restype = ctypes.c_char_p
+        lib.orqa_last_error.argtypes = [vp]
+        lib.orqa_destroy.restype = None
+        lib.orqa_destroy.argtypes = [vp]
+        _lib = lib
+    return _lib
+
+
+def words_per_plane(n_qubits: int) -> int:
+    return 1 if n_qubits <= 64 else 2
+
+
+def strings_from_labels(labels, n_qubits: int):
+    """(x, z) uint64 planes [N, W] of Pauli labels (character q = qubit q)."""
+    W = words_per_plane(n_qubits)
+    x = np.zeros((len(labels), W), dtype=np.uint64)
+    z = np.zeros((len(labels), W), dtype=np.uint64)
+    for i, lab in enumerate(labels):
+        for q, ch in enumerate(lab):
+            bit = np.uint64(1) << np.uint64(q % 64)
+            if ch in "XY":
+                x[i, q // 64] |= bit
+            if ch in "ZY":
+                z[i, q // 64] |= bit
+    return x, z
+
+
+def gate_array(gates):
+    """orqa_gate[] from workload tuples (kind, q0, q1, theta)."""
+    arr = (orqa_gate * len(gates))()
+    for k, (kind, q0, q1, theta) in enumerate(gates):
+        arr[k].kind = {"rx": ORQA_RX, "rzz": ORQA_RZZ}[kind]
+        arr[k].q0 = int(q0)
+        arr[k].q1 = int(q1) if q1 is not None else 0
+        arr[k].pad = 0
+        arr[k].theta = float(theta)
+    return arr
+
+
+def _check(ctx, status):
+    if status != ORQA_OK:
+        msg = library().orqa_last_error(ctx).decode() if ctx else ""
+        raise OrqaError(status, msg)
+
+
+# --- the C entry points, same names -----------------------------------------
+
+def orqa_workspace_bytes(n_qubits: int, capacity: int) -> int:
+    return int(library().orqa_workspace_bytes(n_qubits, capacity))
+
+
+def orqa_create(n_qubits: int, capacity: int, workspace_ptr: int, workspace_bytes: int,
+                stream_ptr: int = 0, flags: int = 0):
+    cfg = orqa_config(n_qubits, flags, capacity, workspace_ptr, workspace_bytes, stream_ptr)
+    h = ctypes.c_void_p()
+    st = library().orqa_create(ctypes.byref(cfg), ctypes.byref(h))
+    if st != ORQA_OK:
+        raise OrqaError(st, "orqa_create")
+    return h
+
+
+def orqa_set_operator(ctx, x: np.ndarray, z: np.ndarray, c: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    _check(ctx, library().orqa_set_operator(ctx, len(c), x.ctypes.data, z.ctypes.data, c.ctypes.data))
+
+
+def orqa_set_operator_device(ctx, x, z, c):
+    """x, z: contiguous int64/uint64 torch tensors [N, W]; c: float64 [N]."""
+    _check(ctx, library().orqa_set_operator_device(ctx, c.numel(), x.data_ptr(), z.data_ptr(),
+                                                   c.data_ptr()))
+
+
+def orqa_apply_layer(ctx, gates, delta: float) -> int:
+    arr = gates if isinstance(gates, ctypes.Array) else gate_array(gates)
+    n = ctypes.c_int64()
+    _check(ctx, library().orqa_apply_layer(ctx, arr, len(arr), float(delta), ctypes.byref(n)))
+    return n.value
+
+
+def orqa_merge_truncate(ctx, delta: float) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, library().orqa_merge_truncate(ctx, float(delta), ctypes.byref(n)))
+    return n.value
+
+
+def orqa_expect(ctx) -> float:
+    out = ctypes.c_double()
+    _check(ctx, library().orqa_expect(ctx, ctypes.byref(out)))
+    return out.value
+
+
+def orqa_export(ctx, n_qubits: int):
+    W = words_per_plane(n_qubits)
+    n = orqa_stats(ctx)["n_strings"]
+    x = np.zeros((max(n, 1), W), dtype=np.uint64)
+    z = np.zeros((max(n, 1), W), dtype=np.uint64)
+    c = np.zeros(max(n, 1), dtype=np.float64)
+    got = ctypes.c_int64()
+    lib = library()
+    _check(ctx, lib.orqa_export(ctx, n, x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(got)))
+    return x[:got.value], z[:got.value], c[:got.value]
+
+
+def orqa_stats(ctx) -> dict:
+    s = orqa_stats_t()
+    _check(ctx, library().orqa_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in orqa_stats_t._fields_ if name != "pad"}
+
+
+def orqa_profile_count() -> int:
+    return int(library().orqa_profile_count())
+
+
+def orqa_profile(ctx, index: int) -> dict:
+    p = orqa_kernel_profile()
+    _check(ctx, library().orqa_profile(ctx, index, ctypes.byref(p)))
+    return {"name": p.name.decode(), "launches": p.launches, "ms": p.ms, "bytes": p.bytes}
+
+
+def orqa_profile_reset(ctx):
+    _check(ctx, library().orqa_profile_reset(ctx))
+
+
+def orqa_last_error(ctx) -> str:
+    return library().orqa_last_error(ctx).decode()
+
+
+def orqa_destroy(ctx):
+    library().orqa_destroy(ctx)
+
+
+# --- convenience wrapper ------------------------------------------------------
+
+class Context:
+    """An operator on the current CUDA device.  The workspace is a torch
+    uint8 tensor owned by this object; work runs on ``stream`` (a
+    torch.cuda.Stream, default: the current stream)."""
+
+    def __init__(self, n_qubits: int, capacity: int, stream=None, device=None, profile: bool = False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liborqa needs a CUDA device; none is available")
+        library()
+        self.n_qubits = n_qubits
+        self.W = words_per_plane(n_qubits)
+        self.capacity = capacity
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            nbytes = orqa_workspace_bytes(n_qubits, capacity)
+            if nbytes == 0:
+                raise ValueError("bad n_qubits / capacity")
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            self.ctx = orqa_create(n_qubits, capacity, aligned, nbytes, self.stream.cuda_stream,
+                                   ORQA_FLAG_PROFILE if profile else 0)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            orqa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_operator(self, x, z, c):
+        orqa_set_operator(self.ctx, x, z, c)
+
+    def set_labels(self, terms):
+        labels = [t[0] for t in terms]
+        x, z = strings_from_labels(labels, self.n_qubits)
+        self.set_operator(x, z, np.array([t[1] for t in terms], dtype=np.float64))
+
+    def set_operator_device(self, x, z, c):
+        orqa_set_operator_device(self.ctx, x, z, c)
+
+    def apply_layer(self, gates, delta: float = 0.0) -> int:
+        return orqa_apply_layer(self.ctx, gates, delta)
+
+    def merge_truncate(self, delta: float = 0.0) -> int:
+        return orqa_merge_truncate(self.ctx, delta)
+
+    def expect(self) -> float:
+        return orqa_expect(self.ctx)
+
+    def export(self):
+        return orqa_export(self.ctx, self.n_qubits)
+
+    def stats(self) -> dict:
+        return orqa_stats(self.ctx)
+
+    def profile(self) -> list:
+        return [orqa_profile(self.ctx, k) for k in range(orqa_profile_count())]
+
+    def profile_reset(self):
+        orqa_profile_reset(self.ctx)
+
+    def __len__(self):
+        return self.stats()["n_strings"]

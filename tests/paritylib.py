@@ -1,0 +1,64 @@
+"""Helpers shared by the parity tests: canonical forms of the CUDA path's
+export (x/z planes) and of the oracle's export (paper multi-index), so the
+two can be compared element by element."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def planes_to_codes(x: np.ndarray, z: np.ndarray, n: int) -> np.ndarray:
+    """Per-site local codes (0 id, 1 x, 2 y, 3 z) [N, n] from x/z planes:
+    the paper's code has high bit z and low bit x xor z."""
+    N = x.shape[0]
+    codes = np.zeros((N, n), dtype=np.uint8)
+    for q in range(n):
+        w, b = divmod(q, 64)
+        xb = ((x[:, w] >> np.uint64(b)) & np.uint64(1)).astype(np.uint8)
+        zb = ((z[:, w] >> np.uint64(b)) & np.uint64(1)).astype(np.uint8)
+        codes[:, q] = (zb << 1) | (xb ^ zb)
+    return codes
+
+
+def index_words_to_codes(keys: np.ndarray, n: int) -> np.ndarray:
+    """Per-site codes [N, n] from oracle multi-index words [N, 4]."""
+    N = keys.shape[0]
+    codes = np.zeros((N, n), dtype=np.uint8)
+    for q in range(n):
+        bit = 2 * q
+        w, b = divmod(bit, 64)
+        codes[:, q] = ((keys[:, w] >> np.uint64(b)) & np.uint64(3)).astype(np.uint8)
+    return codes
+
+
+def canonical(codes: np.ndarray, coef: np.ndarray):
+    """Rows sorted lexicographically by code string."""
+    if codes.shape[0] == 0:
+        return codes, coef
+    order = np.lexsort(codes.T[::-1])
+    return codes[order], coef[order]
+
+
+def gpu_canonical(ctx, n: int):
+    x, z, c = ctx.export()
+    return canonical(planes_to_codes(x, z, n), c)
+
+
+def oracle_canonical(op, n: int):
+    keys, c = op.export()
+    return canonical(index_words_to_codes(keys, n), c)
+
+
+def assert_bit_exact(gpu, ora, what=""):
+    gc, gv = gpu
+    oc, ov = ora
+    assert gc.shape == oc.shape, "%s: |O| gpu %d vs oracle %d" % (what, gc.shape[0], oc.shape[0])
+    if gc.shape[0]:
+        same_keys = np.all(gc == oc, axis=1)
+        assert same_keys.all(), "%s: first differing string at row %d" % (what, int(np.argmin(same_keys)))
+        bad = np.nonzero(gv.view(np.uint64) != ov.view(np.uint64))[0]
+        assert bad.size == 0, "%s: %d coefficients differ, first row %d: %r vs %r" % (
+            what, bad.size, bad[0], gv[bad[0]], ov[bad[0]])
+
+
+def codes_to_labels(codes: np.ndarray):
+    return ["".join("IXYZ"[a] for a in row) for row in codes]

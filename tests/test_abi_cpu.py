@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads and
+exports every entry point include/orqa.h declares, and the argument checks
+that run before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_13241_gb300 import build, orqa
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "orqa.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return orqa.library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(orqa_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    assert names == sorted(orqa.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_workspace_bytes_is_monotone_and_rejects_bad_sizes(lib):
+    assert orqa.orqa_workspace_bytes(0, 10) == 0
+    assert orqa.orqa_workspace_bytes(129, 10) == 0
+    assert orqa.orqa_workspace_bytes(12, 0) == 0
+    a = orqa.orqa_workspace_bytes(64, 1000)
+    b = orqa.orqa_workspace_bytes(65, 1000)
+    c = orqa.orqa_workspace_bytes(65, 100000)
+    assert 0 < a < b < c
+    assert a % 256 == 0 and b % 256 == 0
+
+
+def test_create_validates_config_before_touching_cuda(lib):
+    h = ctypes.c_void_p()
+    assert lib.orqa_create(None, ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, 0, 100, 0, 0, 0)       # null workspace
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, 0, 100, 256 + 3, 1 << 20, 0)  # misaligned
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, 0, 100, 4096, 10, 0)    # too small
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_ENOMEM
+    cfg = orqa.orqa_config(12, 2, 100, 4096, 1 << 30, 0)  # unknown flag bit
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+
+
+def test_gate_array_marshalling():
+    arr = orqa.gate_array([("rx", 3, None, 0.5), ("rzz", 1, 2, -1.5)])
+    assert (arr[0].kind, arr[0].q0, arr[0].theta) == (orqa.ORQA_RX, 3, 0.5)
+    assert (arr[1].kind, arr[1].q0, arr[1].q1) == (orqa.ORQA_RZZ, 1, 2)
+    assert ctypes.sizeof(orqa.orqa_gate) == 24
+    assert ctypes.sizeof(orqa.orqa_config) == 40
+    assert ctypes.sizeof(orqa.orqa_stats_t) == 56
+
+
+def test_label_encoding_matches_paper_codes():
+    """x/z planes re-code the paper's two-bit index (z = high bit,
+    x = high xor low)."""
+    from paritylib import planes_to_codes
+    x, z = orqa.strings_from_labels(["IXYZ" * 20], 80)
+    codes = planes_to_codes(x, z, 80)
+    assert list(codes[0][:4]) == [0, 1, 2, 3]
