@@ -172,6 +172,28 @@ const char* orqa_last_error(const orqa_ctx* ctx);
 /* Releases the host context (the caller's workspace is not freed). */
 void orqa_destroy(orqa_ctx* ctx);
 
+/* Largest operator orqa_expect_noalloc accepts (2^27 strings). */
+#define ORQA_NOALLOC_MAX_STRINGS 134217728LL
+
+/* <0|O|0> of an operator held in caller-owned DEVICE arrays, without a
+ * context and without allocating any device memory.  This entry point has
+ * no counterpart in the paper; it exists for callers that cannot call
+ * cudaMalloc: code embedded in a host framework whose allocator owns the
+ * device memory pool, and latency-critical paths that cannot accept the
+ * device-wide synchronisation an allocation may imply.
+ *   x: n*W words (string-major, as in orqa_set_operator), c: n doubles, both
+ *      on the current device; out: HOST pointer receiving the sum of c over
+ *      strings whose x plane is zero, in FP64.  Waits for `stream`.
+ * Scratch is a fixed file-scope device array (65537 doubles) that every GPU
+ * loading the library holds until exit.  The first call on a device looks up
+ * that array's device address, so it should come before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU race and
+ * must be serialised by the caller.
+ * Returns ORQA_ECAPACITY (nothing launched) if n > ORQA_NOALLOC_MAX_STRINGS,
+ * ORQA_EINVAL for bad arguments, ORQA_ECUDA if a CUDA call fails. */
+orqa_status orqa_expect_noalloc(int32_t n_qubits, int64_t n, const uint64_t* x, const double* c,
+                                double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

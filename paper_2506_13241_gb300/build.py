@@ -1,7 +1,7 @@
 """Builds liborqa.so in-tree with nvcc for sm_103a (GB300).
 
-The library is one CUDA translation unit plus the C ABI header in
-``include/``.  ``-fmad=false`` keeps every coefficient product and sum
+The library is the CUDA translation units in ``csrc/`` plus the C ABI
+header in ``include/``.  ``-fmad=false`` keeps every coefficient product and sum
 separately rounded (the kernels also use explicit _rn intrinsics), so the
 arithmetic matches a CPU evaluation of the per-gate update bit for bit.
 """
@@ -30,10 +30,14 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def translation_units():
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
 def nvcc_cmd(out: str, extra=()):
     return ["nvcc", ARCH, "-O3", "-lineinfo", "-fmad=false", "-std=c++17",
             "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE, *extra,
-            "-o", out, os.path.join(CSRC, "orqa.cu")]
+            "-o", out, *translation_units()]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

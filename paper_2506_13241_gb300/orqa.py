@@ -24,7 +24,8 @@ ORQA_FLAG_PROFILE = 1
 EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_set_operator_device",
             "orqa_apply_layer", "orqa_merge_truncate", "orqa_expect", "orqa_export", "orqa_stats",
             "orqa_profile_count", "orqa_profile", "orqa_profile_reset",
-            "orqa_last_error", "orqa_destroy"]
+            "orqa_last_error", "orqa_destroy", "orqa_expect_noalloc"]
+ORQA_NOALLOC_MAX_STRINGS = 1 << 27
 
 
 class orqa_gate(ctypes.Structure):
@@ -98,6 +99,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_last_error.argtypes = [vp]
         lib.orqa_destroy.restype = None
         lib.orqa_destroy.argtypes = [vp]
+        lib.orqa_expect_noalloc.restype = i32
+        lib.orqa_expect_noalloc.argtypes = [i32, i64, vp, vp, dpp, vp]
         _lib = lib
     return _lib
 
@@ -227,6 +230,16 @@ def orqa_last_error(ctx) -> str:
 
 def orqa_destroy(ctx):
     library().orqa_destroy(ctx)
+
+
+def orqa_expect_noalloc(n_qubits: int, n: int, x_ptr: int, c_ptr: int, stream_ptr: int = 0) -> float:
+    """<0|O|0> of caller-owned device arrays (x: n*W words, c: n doubles),
+    computed without a context and without any device allocation."""
+    out = ctypes.c_double()
+    st = library().orqa_expect_noalloc(n_qubits, n, x_ptr, c_ptr, ctypes.byref(out), stream_ptr)
+    if st != ORQA_OK:
+        raise OrqaError(st, "orqa_expect_noalloc (n=%d, limit %d)" % (n, ORQA_NOALLOC_MAX_STRINGS))
+    return out.value
 
 
 # --- convenience wrapper ------------------------------------------------------
