@@ -1,5 +1,5 @@
 // liborqa: C ABI (include/orqa.h) and host orchestration of the kernels in
-// orqa_kernels.cuh.  The host side validates arguments, carves the caller's
+// orqa_kernels.cuh and orqa_layer.cuh.  The host side validates arguments, carves the caller's
 // workspace, computes cos/sin of each gate once, launches kernels on the
 // caller's stream and reads back small counters; every per-string step runs
 // on the device.
@@ -12,17 +12,18 @@
 
 #include "orqa.h"
 #include "orqa_kernels.cuh"
+#include "orqa_layer.cuh"
 
 using namespace orqa;
 
 namespace {
 enum KernelKind {
-    K_RZZ, K_TRUNCATE, K_SPLIT, K_ASSIGN, K_OFFSETS, K_SCATTER, K_PROCESS,
-    K_MERGE_ASSIGN, K_MERGE_REDUCE, K_EXPECT, K_COUNT
+    K_RZZ, K_TRUNCATE, K_SPLIT, K_SCAN, K_BUCKET_SCATTER, K_LOCAL,
+    K_MERGE_ASSIGN, K_MERGE_OFFSETS, K_MERGE_SCATTER, K_MERGE_REDUCE, K_EXPECT, K_COUNT
 };
 const char* const KERNEL_NAMES[K_COUNT] = {
-    "rzz_layer", "truncate", "rx_split", "unit_assign", "unit_offsets", "unit_scatter",
-    "unit_process", "merge_assign", "merge_reduce", "expect"};
+    "rzz_layer", "truncate", "rx_split", "fine_scan", "bucket_scatter", "unit_local",
+    "merge_assign", "merge_offsets", "merge_scatter", "merge_reduce", "expect"};
 
 struct PendingLaunch {
     int kind;
@@ -38,22 +39,31 @@ struct orqa_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 1;
 
-    StrList buf[4];
+    StrList buf[3];
     int cur = 0;            // buffer holding the operator
     long long n = 0;        // |O|
     double clean_delta = 0; // no live coefficient is below this
 
+    // duplicate merge (global hash table)
     int32_t* uid = nullptr;
     int32_t* rank = nullptr;
-    uint8_t* idx = nullptr;
     uint64_t* unit_z = nullptr;
     uint64_t* unit_xb = nullptr;
     int32_t* unit_count = nullptr;
     long long* unit_off = nullptr;
     double* sorted_c = nullptr;
-    uint8_t* sorted_idx = nullptr;
     int32_t* table = nullptr;
     long long table_cap = 0;
+    // X-layer passes (fine buckets)
+    int n_fine = 0;
+    int fshift = 0;
+    int32_t* fcount[2] = {nullptr, nullptr};
+    long long* foffsets = nullptr;
+    long long* fcursor = nullptr;
+    long long* tile_sums = nullptr;
+    uint64_t* hash_active = nullptr;   // unit-key hashes of the active list
+    void* records = nullptr;           // bucket-ordered copy of the active list
+    size_t local_smem = 0;
     Counters* ctr = nullptr;
     unsigned long long* pop_delta = nullptr;
     double* partials = nullptr;
@@ -96,7 +106,16 @@ struct Layout {
     size_t str_x, str_c;  // per string buffer: x and z planes, c
     size_t total;
     long long table_cap;
+    long long n_fine;
 };
+
+// Fine buckets: about 32 strings each at full capacity, a power of two and a
+// multiple of the scan tile, at most SCAN_TILE tiles.
+long long fine_buckets(long long cap) {
+    long long f = SCAN_TILE;
+    while (f < cap / 32 && f < (long long)SCAN_TILE * SCAN_TILE) f <<= 1;
+    return f;
+}
 
 // Offsets are computed in the same order by workspace_bytes and carve().
 Layout layout(int n_qubits, long long cap) {
@@ -106,16 +125,22 @@ Layout layout(int n_qubits, long long cap) {
     L.str_x = align_up(C * W * 8);
     L.str_c = align_up(C * 8);
     L.table_cap = pow2_at_least(2 * cap);
+    L.n_fine = fine_buckets(cap);
+    const size_t F = (size_t)L.n_fine;
     size_t t = 0;
-    t += 4 * (2 * L.str_x + L.str_c);     // four string buffers
+    t += 3 * (2 * L.str_x + L.str_c);     // three string buffers
     t += 2 * align_up(C * 4);              // uid, rank
-    t += align_up(C);                      // idx
     t += 2 * L.str_x;                      // unit_z, unit_xb
     t += align_up(C * 4);                  // unit_count
     t += align_up(C * 8);                  // unit_off
     t += align_up(C * 8);                  // sorted_c
-    t += align_up(C);                      // sorted_idx
     t += align_up((size_t)L.table_cap * 4);  // hash table
+    t += 2 * align_up(F * 4);              // fine counts (two passes)
+    t += align_up((F + 1) * 8);            // fine offsets
+    t += align_up(F * 8);                  // fine cursors
+    t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
+    t += align_up(C * 8);                  // unit-key hashes of the active list
+    t += align_up(C * (size_t)record_bytes(W));  // bucket records
     t += align_up(sizeof(Counters));
     t += align_up(MAX_QUBITS * 8);
     t += align_up(EXPECT_BLOCKS * 8);
@@ -240,7 +265,6 @@ orqa_status check_flags(orqa_ctx* ctx, const Counters& h, const char* what) {
 template <int W>
 orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, double delta,
                        long long* n_out) {
-    RxRun run{};  // unused in full-key mode
     const long long tcap = pow2_at_least(2 * (n > 0 ? n : 1));
     if (tcap > ctx->table_cap) return fail(ctx, ORQA_ECAPACITY, "merge: hash table too small");
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
@@ -249,24 +273,21 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->table, 0xff, (size_t)tcap * 4, ctx->stream));
         const int g = grid_for(ctx, n);
         r_as = prof_begin(ctx, K_MERGE_ASSIGN, 0);
-        k_unit_assign<W, true><<<g, 256, 0, ctx->stream>>>(src, n, run, 0, ctx->table, tcap - 1,
-                                                           ctx->unit_z, ctx->unit_xb, ctx->unit_count,
-                                                           ctx->uid, ctx->rank, ctx->idx, ctx->ctr);
+        k_merge_assign<W><<<g, 256, 0, ctx->stream>>>(src, n, ctx->table, tcap - 1, ctx->unit_z, ctx->unit_xb,
+                                                       ctx->unit_count, ctx->uid, ctx->rank, ctx->ctr);
         prof_end(ctx, r_as);
         LAUNCH_CHECK(ctx);
-        r_off = prof_begin(ctx, K_OFFSETS, 0);
-        k_unit_offsets<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(ctx->unit_count, ctx->unit_off, ctx->ctr);
+        r_off = prof_begin(ctx, K_MERGE_OFFSETS, 0);
+        k_merge_offsets<<<g, 256, 0, ctx->stream>>>(ctx->unit_count, ctx->unit_off, ctx->ctr);
         prof_end(ctx, r_off);
         LAUNCH_CHECK(ctx);
-        r_sc = prof_begin(ctx, K_SCATTER, 0);
-        k_unit_scatter<false><<<g, 256, 0, ctx->stream>>>(src.c, n, ctx->uid, ctx->rank, ctx->idx,
-                                                          ctx->unit_off, ctx->sorted_c, ctx->sorted_idx);
+        r_sc = prof_begin(ctx, K_MERGE_SCATTER, (double)n * 32.0);
+        k_merge_scatter<<<g, 256, 0, ctx->stream>>>(src.c, n, ctx->uid, ctx->rank, ctx->unit_off, ctx->sorted_c);
         prof_end(ctx, r_sc);
         LAUNCH_CHECK(ctx);
         r_red = prof_begin(ctx, K_MERGE_REDUCE, 0);
-        k_merge_reduce<W><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(
-            ctx->unit_z, ctx->unit_xb, ctx->unit_count, ctx->unit_off, ctx->sorted_c, delta,
-            ctx->buf[dst_buf], ctx->cap, ctx->ctr);
+        k_merge_reduce<W><<<g, 256, 0, ctx->stream>>>(ctx->unit_z, ctx->unit_xb, ctx->unit_count, ctx->unit_off,
+                                                       ctx->sorted_c, delta, ctx->buf[dst_buf], ctx->cap, ctx->ctr);
         prof_end(ctx, r_red);
         LAUNCH_CHECK(ctx);
     }
@@ -275,9 +296,8 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
     if (st != ORQA_OK) return st;
     {
         const double R = 8.0 * (2 * W + 1), nu = (double)h.n_units, nn = (double)n;
-        prof_set_bytes(ctx, r_as, nn * (32.0 * W + 13.0) + nu * (16.0 * W + 4.0));
+        prof_set_bytes(ctx, r_as, nn * (32.0 * W + 12.0) + nu * (16.0 * W + 4.0));
         prof_set_bytes(ctx, r_off, nu * 12.0);
-        prof_set_bytes(ctx, r_sc, nn * 32.0);
         prof_set_bytes(ctx, r_red, nu * (16.0 * W + 12.0) + nn * 8.0 + (double)h.n_done * R);
         prof_resolve(ctx);
     }
@@ -328,7 +348,7 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     ctx->stats.dropped = 0;
     ctx->stats.chunk_passes = 0;
     if (delta > ctx->clean_delta && ctx->n > 0) {
-        const int dst = (ctx->cur + 1) % 4;
+        const int dst = (ctx->cur + 1) % 3;
         if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
         const int r = prof_begin(ctx, K_TRUNCATE, 0);
         k_truncate<W><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, ctx->buf[dst], ctx->cap,
@@ -349,6 +369,18 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     return ORQA_OK;
 }
 
+// Exclusive scan of fine-bucket counts fcount[k] into foffsets / fcursor.
+orqa_status fine_scan(orqa_ctx* ctx, int k) {
+    const int tiles = ctx->n_fine / SCAN_TILE;
+    const int r = prof_begin(ctx, K_SCAN, (double)ctx->n_fine * 28.0);
+    k_scan_tiles<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->fcount[k], ctx->foffsets, ctx->tile_sums);
+    k_scan_top<<<1, SCAN_THREADS, 0, ctx->stream>>>(ctx->tile_sums, tiles);
+    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->fcursor, ctx->tile_sums, ctx->n_fine);
+    prof_end(ctx, r);
+    LAUNCH_CHECK(ctx);
+    return ORQA_OK;
+}
+
 template <int W>
 orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     RxRun run{};
@@ -362,77 +394,63 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         bool cl;
         cos_sin(g[k].theta, &run.cs[q], &run.sn[q], &cl);
     }
+    const double R = 8.0 * (2 * W + 1);
     const int S = ctx->cur;
-    const int D = (S + 1) % 4, A0 = (S + 2) % 4, A1 = (S + 3) % 4;
+    const int D = (S + 1) % 3;
+    StrList act = ctx->buf[(S + 2) % 3];
+    act.h = ctx->hash_active;
     const long long n_in = ctx->n;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
-    const double R = 8.0 * (2 * W + 1);
+    int fc = 0;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount[fc], 0, (size_t)ctx->n_fine * 4, ctx->stream));
     int r_split = -1;
     if (n_in > 0) {
         r_split = prof_begin(ctx, K_SPLIT, 0);
-        k_rx_split<W><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[S], n_in, ctx->buf[D],
-                                                                   ctx->buf[A0], ctx->cap, run, ctx->ctr);
+        k_rx_split<W><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[S], n_in, ctx->buf[D], act,
+                                                                   ctx->cap, run, ctx->ctr, ctx->fcount[fc],
+                                                                   ctx->fshift);
         prof_end(ctx, r_split);
         LAUNCH_CHECK(ctx);
     }
     Counters h{};
     orqa_status st = sync_counters(ctx, &h);
     if (st != ORQA_OK) return st;
-    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + 8.0) + (double)(h.n_done + h.n_next) * (8.0 * W + R));
+    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + 8.0) + (double)(h.n_done + h.n_next) * (8.0 * W + R) +
+                                     (double)h.n_next * 8.0);
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
     const unsigned long long split_dropped = h.dropped;
     long long n_active = (long long)h.n_next;
     long long peak = (long long)h.n_done + n_active;
-    int a_cur = A0, a_next = A1;
     int pass = 0;
-    const int g_units = ctx->sm_count * 8;
     while (n_active > 0) {
-        const long long tcap = pow2_at_least(2 * n_active);
-        if (tcap > ctx->table_cap) return fail(ctx, ORQA_ECAPACITY, "rotation layer: hash table too small");
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->table, 0xff, (size_t)tcap * 4, ctx->stream));
-        // fresh unit bookkeeping and next-list cursor for this pass
-        CUDA_TRY(ctx, cudaMemsetAsync(&ctx->ctr->n_next, 0, 3 * sizeof(unsigned long long), ctx->stream));
-        const int g = grid_for(ctx, n_active);
+        if ((st = fine_scan(ctx, fc)) != ORQA_OK) return st;
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount[fc ^ 1], 0, (size_t)ctx->n_fine * 4, ctx->stream));
+        CUDA_TRY(ctx, cudaMemsetAsync(&ctx->ctr->n_next, 0, sizeof(unsigned long long), ctx->stream));
         const unsigned long long done_before = h.n_done;
-        const int r_as = prof_begin(ctx, K_ASSIGN, 0);
-        k_unit_assign<W, false><<<g, 256, 0, ctx->stream>>>(
-            ctx->buf[a_cur], n_active, run, pass, ctx->table, tcap - 1, ctx->unit_z, ctx->unit_xb,
-            ctx->unit_count, ctx->uid, ctx->rank, ctx->idx, ctx->ctr);
-        prof_end(ctx, r_as);
-        LAUNCH_CHECK(ctx);
-        const int r_off = prof_begin(ctx, K_OFFSETS, 0);
-        k_unit_offsets<<<g, 256, 0, ctx->stream>>>(ctx->unit_count, ctx->unit_off, ctx->ctr);
-        prof_end(ctx, r_off);
-        LAUNCH_CHECK(ctx);
-        const int r_sc = prof_begin(ctx, K_SCATTER, (double)n_active * 34.0);
-        k_unit_scatter<true><<<g, 256, 0, ctx->stream>>>(ctx->buf[a_cur].c, n_active, ctx->uid, ctx->rank,
-                                                         ctx->idx, ctx->unit_off, ctx->sorted_c,
-                                                         ctx->sorted_idx);
+        const int r_sc = prof_begin(ctx, K_BUCKET_SCATTER, (double)n_active * (R + 8.0 + record_bytes(W)));
+        k_bucket_scatter<W><<<grid_for(ctx, (n_active + SCATTER_ILP - 1) / SCATTER_ILP), 256, 0, ctx->stream>>>(
+            act, n_active, ctx->fshift, ctx->fcursor, ctx->records);
         prof_end(ctx, r_sc);
         LAUNCH_CHECK(ctx);
-        const int r_pr = prof_begin(ctx, K_PROCESS, 0);
-        k_unit_process<W><<<g_units, PROCESS_WARPS * 32, 0, ctx->stream>>>(
-            ctx->unit_z, ctx->unit_xb, ctx->unit_count, ctx->unit_off, ctx->sorted_c, ctx->sorted_idx,
-            run, pass, ctx->buf[D], ctx->buf[a_next], ctx->cap, ctx->ctr, ctx->pop_delta);
-        prof_end(ctx, r_pr);
+        const long long ranges = (n_active + LB_TARGET - 1) / LB_TARGET;
+        const int r_lo = prof_begin(ctx, K_LOCAL, 0);
+        k_bucket_local<W><<<(unsigned)ranges, LB_THREADS, ctx->local_smem, ctx->stream>>>(
+            ctx->records, ctx->foffsets, ctx->n_fine, run, pass, ctx->buf[D], act, ctx->cap, ctx->ctr,
+            ctx->fcount[fc ^ 1], ctx->fshift, ctx->pop_delta);
+        prof_end(ctx, r_lo);
         LAUNCH_CHECK(ctx);
         if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
-        {
-            const double nu = (double)h.n_units, na = (double)n_active;
-            const double outs = (double)(h.n_done - done_before) + (double)h.n_next;
-            prof_set_bytes(ctx, r_as, na * (32.0 * W + 13.0) + nu * (16.0 * W + 4.0));
-            prof_set_bytes(ctx, r_off, nu * 12.0);
-            prof_set_bytes(ctx, r_pr, nu * (16.0 * W + 12.0) + na * 9.0 + outs * R);
-            prof_resolve(ctx);
-        }
+        const double outs = (double)(h.n_done - done_before) + (double)h.n_next;
+        prof_set_bytes(ctx, r_lo, (double)n_active * record_bytes(W) + outs * R + (double)h.n_next * 8.0);
+        prof_resolve(ctx);
         if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
+        if (h.bucket_overflow)
+            return fail(ctx, ORQA_ECAPACITY, "rotation layer: a bucket range exceeded the shared-memory capacity");
         n_active = (long long)h.n_next;
         if ((long long)h.n_done + n_active > peak) peak = (long long)h.n_done + n_active;
-        const int t = a_cur;
-        a_cur = a_next;
-        a_next = t;
+        fc ^= 1;
         ++pass;
     }
     // Sum over the gates of |O| before each gate: |O| changes at gate q by
@@ -480,7 +498,7 @@ orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t
     if (n < 0 || (n > 0 && (!x || !z || !c))) return fail(ctx, ORQA_EINVAL, "set_operator: bad arguments");
     if (n > ctx->cap) return fail(ctx, ORQA_ECAPACITY, "set_operator: n exceeds capacity");
     const int W = ctx->W;
-    const int stage = (ctx->cur + 1) % 4, dst = (ctx->cur + 2) % 4;
+    const int stage = (ctx->cur + 1) % 3, dst = (ctx->cur + 2) % 3;
     StrList s = ctx->buf[stage];
     if (n > 0) {
         CUDA_TRY(ctx, cudaMemcpyAsync(s.x, x, (size_t)n * W * 8, kind, ctx->stream));
@@ -529,26 +547,45 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     }
     char* p = (char*)cfg->workspace;
     const size_t C = (size_t)cfg->capacity;
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < 3; ++b) {
         ctx->buf[b].x = (uint64_t*)p; p += L.str_x;
         ctx->buf[b].z = (uint64_t*)p; p += L.str_x;
         ctx->buf[b].c = (double*)p;   p += L.str_c;
+        ctx->buf[b].h = nullptr;
     }
     ctx->uid = (int32_t*)p; p += align_up(C * 4);
     ctx->rank = (int32_t*)p; p += align_up(C * 4);
-    ctx->idx = (uint8_t*)p; p += align_up(C);
     ctx->unit_z = (uint64_t*)p; p += L.str_x;
     ctx->unit_xb = (uint64_t*)p; p += L.str_x;
     ctx->unit_count = (int32_t*)p; p += align_up(C * 4);
     ctx->unit_off = (long long*)p; p += align_up(C * 8);
     ctx->sorted_c = (double*)p; p += align_up(C * 8);
-    ctx->sorted_idx = (uint8_t*)p; p += align_up(C);
     ctx->table = (int32_t*)p; p += align_up((size_t)L.table_cap * 4);
     ctx->table_cap = L.table_cap;
+    const size_t F = (size_t)L.n_fine;
+    ctx->n_fine = (int)L.n_fine;
+    ctx->fshift = 64 - __builtin_ctzll((unsigned long long)L.n_fine);
+    ctx->fcount[0] = (int32_t*)p; p += align_up(F * 4);
+    ctx->fcount[1] = (int32_t*)p; p += align_up(F * 4);
+    ctx->foffsets = (long long*)p; p += align_up((F + 1) * 8);
+    ctx->fcursor = (long long*)p; p += align_up(F * 8);
+    ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
+    ctx->hash_active = (uint64_t*)p; p += align_up(C * 8);
+    ctx->records = (void*)p; p += align_up(C * (size_t)record_bytes(ctx->W));
     ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));
     ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
     ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);
     ctx->scalar = (double*)p; p += align_up(64);
+    ctx->local_smem = (ctx->W == 1) ? sizeof(LocalSmem<1>) : sizeof(LocalSmem<2>);
+    cudaError_t fe = (ctx->W == 1)
+                         ? cudaFuncSetAttribute(k_bucket_local<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)ctx->local_smem)
+                         : cudaFuncSetAttribute(k_bucket_local<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)ctx->local_smem);
+    if (fe != cudaSuccess) {
+        delete ctx;
+        return ORQA_ECUDA;
+    }
     *out = ctx;
     return ORQA_OK;
 }
@@ -597,7 +634,7 @@ orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_ga
 orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out) {
     if (!ctx) return ORQA_EINVAL;
     if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "merge_truncate: bad delta");
-    const int dst = (ctx->cur + 1) % 4;
+    const int dst = (ctx->cur + 1) % 3;
     long long m = 0;
     orqa_status st = (ctx->W == 1) ? merge_into<1>(ctx, ctx->buf[ctx->cur], ctx->n, dst, delta, &m)
                                    : merge_into<2>(ctx, ctx->buf[ctx->cur], ctx->n, dst, delta, &m);

@@ -23,6 +23,7 @@ struct StrList {
     uint64_t* x;
     uint64_t* z;
     double* c;
+    uint64_t* h;  // per-string unit-key hash for the next chunk pass (layer lists only)
 };
 
 // Device counters shared by the kernels of one call.
@@ -36,7 +37,7 @@ struct Counters {
     unsigned int overflow;           // an append would have exceeded capacity
     unsigned int timeout;            // a bounded spin-wait gave up
     unsigned int table_full;         // the hash table had no free slot
-    unsigned int pad;
+    unsigned int bucket_overflow;    // a CTA range exceeded its shared-memory capacity
     double expect_partial[1];        // unused placeholder (keeps 8-byte alignment)
 };
 
@@ -99,6 +100,57 @@ __device__ __forceinline__ int get_bit(const uint64_t* v, int q) {
     return (int)((v[q >> 6] >> (q & 63)) & 1ull);
 }
 
+// Register-only bit access for W-word planes (no dynamic array indexing, so
+// the planes stay in registers).
+template <int W>
+__device__ __forceinline__ int bit_of(const uint64_t (&v)[W], int q) {
+    if constexpr (W == 1) {
+        return (int)((v[0] >> q) & 1ull);
+    } else {
+        const uint64_t w = (q < 64) ? v[0] : v[1];
+        return (int)((w >> (q & 63)) & 1ull);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void xor_bit(uint64_t (&v)[W], int q) {
+    if constexpr (W == 1) {
+        v[0] ^= 1ull << q;
+    } else {
+        const uint64_t b = 1ull << (q & 63);
+        if (q < 64)
+            v[0] ^= b;
+        else
+            v[1] ^= b;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void set_bit(uint64_t (&v)[W], int q) {
+    if constexpr (W == 1) {
+        v[0] |= 1ull << q;
+    } else {
+        const uint64_t b = 1ull << (q & 63);
+        if (q < 64)
+            v[0] |= b;
+        else
+            v[1] |= b;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void clear_bit(uint64_t (&v)[W], int q) {
+    if constexpr (W == 1) {
+        v[0] &= ~(1ull << q);
+    } else {
+        const uint64_t b = ~(1ull << (q & 63));
+        if (q < 64)
+            v[0] &= b;
+        else
+            v[1] &= b;
+    }
+}
+
 template <int W>
 __device__ __forceinline__ bool all_zero(const uint64_t (&v)[W]) {
     uint64_t acc = 0;
@@ -116,15 +168,55 @@ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
     return h;
 }
 
+// Hash of a (z, x) key: one odd-constant multiply per word, then the mix64
+// finaliser, whose top bits pick fine buckets and low bits pick shared-memory
+// slots.  Equality is always decided on the full key.
 template <int W>
 __device__ __forceinline__ uint64_t hash_key(const uint64_t (&z)[W], const uint64_t (&xb)[W]) {
-    uint64_t h = 0x9e3779b97f4a7c15ull;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        h = mix64(h ^ z[w]) + 0x632be59bd9b4e019ull;
-        h = mix64(h ^ xb[w]) + 0x2545f4914f6cdd1dull;
+    uint64_t h = z[0] * 0x9e3779b97f4a7c15ull ^ (xb[0] * 0xc2b2ae3d27d4eb4full + 0x165667b19e3779f9ull);
+    if constexpr (W == 2) {
+        h ^= (z[1] * 0xd6e8feb86659fd93ull) ^ ((xb[1] * 0x94d049bb133111ebull) >> 1);
+        h += 0x27d4eb2f165667c5ull;
     }
-    return h;
+    return mix64(h);
+}
+
+// Position of the k-th set bit (0-based, k < popcount(v)) of v.
+__device__ __forceinline__ int nth_set_bit(uint64_t v, int k) {
+    int pos = 0;
+    int c = __popc((unsigned)v);
+    if (k >= c) {
+        k -= c;
+        v >>= 32;
+        pos = 32;
+    }
+    unsigned w = (unsigned)v;
+    c = __popc(w & 0xffffu);
+    if (k >= c) {
+        k -= c;
+        w >>= 16;
+        pos += 16;
+    }
+    c = __popc(w & 0xffu);
+    if (k >= c) {
+        k -= c;
+        w >>= 8;
+        pos += 8;
+    }
+    c = __popc(w & 0xfu);
+    if (k >= c) {
+        k -= c;
+        w >>= 4;
+        pos += 4;
+    }
+    c = __popc(w & 0x3u);
+    if (k >= c) {
+        k -= c;
+        w >>= 2;
+        pos += 2;
+    }
+    if (k >= (int)(w & 1u)) pos += 1;
+    return pos;
 }
 
 // Positions (ascending) of the set bits of f whose rank among the set bits
@@ -138,18 +230,18 @@ __device__ __forceinline__ int chunk_positions(const uint64_t (&f)[W], int skip,
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         uint64_t v = f[w];
-        int cnt = __popcll(v);
         if (r == CHUNK_BITS) {
             more = more || (v != 0);
             continue;
         }
+        const int cnt = __popcll(v);
         if (skip >= cnt) {
             skip -= cnt;
             continue;
         }
-        while (skip > 0) {
-            v &= v - 1;
-            --skip;
+        if (skip > 0) {
+            v &= ~((1ull << nth_set_bit(v, skip)) - 1ull);
+            skip = 0;
         }
         while (v != 0 && r < CHUNK_BITS) {
             pos[r++] = 64 * w + (__ffsll((long long)v) - 1);
@@ -158,6 +250,30 @@ __device__ __forceinline__ int chunk_positions(const uint64_t (&f)[W], int skip,
         if (v != 0) more = true;
     }
     return r;
+}
+
+// Unit key of a string for chunk pass `pass` of an X-rotation run: z and x
+// with the chunk's bits cleared (see the unit definition in the layer
+// kernels).  Returns its 64-bit hash; fills the chunk's qubit positions,
+// their count, the string's packed chunk index and whether F has bits
+// beyond the chunk.
+template <int W>
+__device__ __forceinline__ uint64_t unit_key_hash(const uint64_t (&x)[W], const uint64_t (&z)[W],
+                                                  const uint64_t* mask, int pass, int (&pos)[CHUNK_BITS],
+                                                  int& np, int& idx, bool& more) {
+    uint64_t f[W], xb[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        f[w] = z[w] & mask[w];
+        xb[w] = x[w];
+    }
+    np = chunk_positions<W>(f, CHUNK_BITS * pass, pos, more);
+    idx = 0;
+    for (int j = 0; j < np; ++j) {
+        idx |= bit_of<W>(x, pos[j]) << j;
+        clear_bit<W>(xb, pos[j]);
+    }
+    return hash_key<W>(z, xb);
 }
 
 // Warp-aggregated append: every lane of a full warp calls it; lanes with

@@ -1,0 +1,674 @@
+// X-rotation layer pipeline (Eq. update_rule applied gate by gate with the
+// truncation of Algorithm 1), organised for GB300.
+//
+// A run of X rotations on ascending qubits (mask M) never changes z, so it
+// acts independently on every group of strings with equal z and equal x
+// outside F = z & M.  Inside a group a string anticommutes exactly with the
+// gates of F.  The run is applied in chunk passes: pass p applies the gates
+// of the F bits of rank [5p, 5p + 5) to "units" -- strings with equal z and
+// equal x outside those <= 5 chunk bits -- so a unit is a dense vector over
+// at most 32 x-patterns and never exchanges coefficients with another unit.
+// Processing the gates of one unit in order with truncation after each is
+// exactly Algorithm 1 restricted to that unit, because the gates outside
+// the unit's chunk act trivially on it and truncation is per string.
+//
+// Each pass:
+//   1. fine-bucket counts of the active strings (filled by the kernel that
+//      wrote them): bucket = top bits of the hash of the unit key;
+//   2. exclusive scan of the counts;
+//   3. one streaming scatter of the active strings into bucket order;
+//   4. one CTA per contiguous range of ~LB_TARGET strings (whole buckets, so
+//      whole units) builds the units in shared memory and updates them there.
+// Survivors are appended to the output list (no chunk left) or to the next
+// active list, whose bucket counts are accumulated on the fly.
+#pragma once
+
+#include "orqa_device.cuh"
+
+namespace orqa {
+
+constexpr int LB_THREADS = 256;
+constexpr int LB_WARPS = LB_THREADS / 32;
+constexpr int LB_MAX = 512;         // most strings one CTA range may hold
+constexpr int LB_TARGET = 320;      // strings per CTA range, on average
+constexpr int LB_TABLE = 1024;      // shared-memory hash slots
+constexpr int LB_UPW = 16;          // units a warp owns per round (lanes 0..15)
+constexpr int LB_RU = LB_WARPS * LB_UPW;  // units per round
+constexpr int LB_LIST = LB_UPW * 16;      // most pairs of one level in a warp
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int)(h >> fshift); }
+
+// ---------------------------------------------------------------------------
+// Entry split of a run (see the header comment): strings with F = 0 only
+// meet the truncation and go to the output list; the others go to the active
+// list.  A string already below delta is removed by the truncation after the
+// run's first gate unless that gate acts on it first.  Active strings are
+// counted into their pass-0 fine bucket.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrList done, StrList active,
+                                                  long long cap, const __grid_constant__ RxRun run,
+                                                  Counters* ctr, int32_t* fcount, int fshift) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_round = (n + 31) & ~31ll;
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(run.delta);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        uint64_t x[W], z[W];
+        double c = 0.0;
+        const bool live = i < n;
+        bool act = false, keep = false;
+        if (live) {
+            load_plane<W>(src.z, i, z);
+            c = src.c[i];
+            uint64_t acc = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc |= z[w] & run.mask[w];
+            act = acc != 0;
+            keep = keep_bits(c, dbits);
+            if (act && !keep) {
+                uint64_t f[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
+                if (!bit_of<W>(f, run.q_first)) act = false;  // dropped before its gates
+            }
+        }
+        const bool to_done = live && !act && keep;
+        const long long sd = warp_append(to_done, &ctr->n_done);
+        const long long sa = warp_append(act, &ctr->n_next);
+        if (to_done || act) {
+            const long long slot = to_done ? sd : sa;
+            StrList dst = to_done ? done : active;
+            load_plane<W>(src.x, i, x);
+            if (slot < cap) {
+                store_plane<W>(dst.x, slot, x);
+                store_plane<W>(dst.z, slot, z);
+                dst.c[slot] = c;
+            } else {
+                ctr->overflow = 1u;
+            }
+            if (act) {
+                int pos[CHUNK_BITS], np, idx;
+                bool more;
+                const uint64_t h = unit_key_hash<W>(x, z, run.mask, 0, pos, np, idx, more);
+                if (slot < cap) active.h[slot] = h;
+                atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
+            }
+        }
+        const unsigned nd = __popc(__ballot_sync(FULL_MASK, live && !act && !keep));
+        if ((threadIdx.x & 31) == 0 && nd) atomicAdd(&ctr->dropped, (unsigned long long)nd);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the fine-bucket counts (n = number of buckets, a
+// multiple of SCAN_TILE): tile sums, a one-block scan of the tile sums,
+// then offsets[b] and cursor[b] = offsets[b]; offsets[n] = total.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& total) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) warp_tot[wp] = incl;
+    __syncthreads();
+    if (wp == 0) {
+        const int nw = blockDim.x >> 5;
+        int t = lane < nw ? warp_tot[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(FULL_MASK, ti, d);
+            if (lane >= d) ti += u;
+        }
+        if (lane < nw) warp_tot[lane] = ti - t;
+        if (lane == nw - 1) warp_tot[32] = ti;
+    }
+    __syncthreads();
+    const int r = warp_tot[wp] + incl - v;
+    total = warp_tot[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int32_t* counts, long long* offsets,
+                                                             long long* tile_sums) {
+    __shared__ int warp_tot[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = counts[base + k];
+        s += v[k];
+    }
+    int total;
+    int run = block_scan_exclusive(s, warp_tot, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        offsets[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// One block; n_tiles <= SCAN_TILE.  All counts fit in int (they sum to at
+// most the capacity, < 2^31).
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums, int n_tiles) {
+    __shared__ int warp_tot[33];
+    const int t = threadIdx.x;
+    int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int i = t * SCAN_ITEMS + k;
+        v[k] = i < n_tiles ? (int)tile_sums[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_scan_exclusive(s, warp_tot, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int i = t * SCAN_ITEMS + k;
+        if (i < n_tiles) tile_sums[i] = run;
+        run += v[k];
+    }
+    if (t == 0) tile_sums[SCAN_TILE] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, long long* cursor,
+                                                           const long long* tile_sums, long long n) {
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    const long long add = tile_sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const long long o = offsets[base + k] + add;
+        offsets[base + k] = o;
+        cursor[base + k] = o;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) offsets[n] = tile_sums[SCAN_TILE];
+}
+
+// ---------------------------------------------------------------------------
+// Scatter of the active strings into fine-bucket order, using the unit-key
+// hash stored with each string.  The bucket-ordered copy is an array of
+// records of whole 32-byte sectors -- (x, z, c, h) padded to 64 bytes for
+// W = 2, exactly 32 bytes for W = 1 -- so the scattered writes never leave a
+// partly written sector.  Eight strings per thread keep eight cursor
+// atomics in flight.
+// ---------------------------------------------------------------------------
+constexpr int SCATTER_ILP = 8;
+
+template <int W>
+__device__ __forceinline__ void store_record(void* base, long long i, const uint64_t (&x)[W],
+                                             const uint64_t (&z)[W], double c, uint64_t h) {
+    if constexpr (W == 2) {
+        ulonglong2* r = reinterpret_cast<ulonglong2*>(base) + 4 * i;
+        r[0] = make_ulonglong2(x[0], x[1]);
+        r[1] = make_ulonglong2(z[0], z[1]);
+        r[2] = make_ulonglong2((unsigned long long)__double_as_longlong(c), h);
+        r[3] = make_ulonglong2(0ull, 0ull);  // completes the second sector
+    } else {
+        ulonglong2* r = reinterpret_cast<ulonglong2*>(base) + 2 * i;
+        r[0] = make_ulonglong2(x[0], z[0]);
+        r[1] = make_ulonglong2((unsigned long long)__double_as_longlong(c), h);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void load_record(const void* base, long long i, uint64_t (&x)[W], uint64_t (&z)[W],
+                                            double& c, uint64_t& h) {
+    if constexpr (W == 2) {
+        const ulonglong2* r = reinterpret_cast<const ulonglong2*>(base) + 4 * i;
+        const ulonglong2 a = r[0], b = r[1], d = r[2];
+        x[0] = a.x;
+        x[1] = a.y;
+        z[0] = b.x;
+        z[1] = b.y;
+        c = __longlong_as_double((long long)d.x);
+        h = d.y;
+    } else {
+        const ulonglong2* r = reinterpret_cast<const ulonglong2*>(base) + 2 * i;
+        const ulonglong2 a = r[0], d = r[1];
+        x[0] = a.x;
+        z[0] = a.y;
+        c = __longlong_as_double((long long)d.x);
+        h = d.y;
+    }
+}
+
+constexpr int record_bytes(int W) { return W == 2 ? 64 : 32; }
+
+template <int W>
+__global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n, int fshift,
+                                                        long long* cursor, void* dst) {
+    const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
+    for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x; base < n;
+         base += stride) {
+        long long slot[SCATTER_ILP];
+        uint64_t h[SCATTER_ILP];
+#pragma unroll
+        for (int k = 0; k < SCATTER_ILP; ++k) {
+            const long long i = base + (long long)k * blockDim.x;
+            h[k] = (i < n) ? src.h[i] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < SCATTER_ILP; ++k) {
+            const long long i = base + (long long)k * blockDim.x;
+            slot[k] = (i < n) ? (long long)atomicAdd((unsigned long long*)&cursor[fine_bucket(h[k], fshift)], 1ull)
+                              : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < SCATTER_ILP; ++k) {
+            const long long i = base + (long long)k * blockDim.x;
+            if (slot[k] < 0) continue;
+            uint64_t x[W], z[W];
+            load_plane<W>(src.x, i, x);
+            load_plane<W>(src.z, i, z);
+            store_record<W>(dst, slot[k], x, z, src.c[i], h[k]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-local unit processing.
+//
+// A CTA loads its range (whole fine buckets, so whole units) into shared
+// memory and groups the strings into units with a shared-memory hash table on
+// the exact key (z, x outside the chunk).  Units are processed LB_RU per
+// round: a unit is a 32-slot row (slot = the string's chunk bits) with a
+// 32-bit occupancy mask.  For chunk level j the pair {slot l, slot l | 2^j}
+// (bit j of l clear) holds the strings P (sigma_z at the level's qubit q) and
+// P xor X_q (sigma_y); by Eq. (update_rule) with B(Z,X) = 1, B(Y,X) = -1,
+//     new c_Z = cos c_Z - sin c_Y,   new c_Y = cos c_Y + sin c_Z,
+// an absent member counting as 0 (Algorithm 1 inserts it), then the
+// truncation c == 0 or |c| < delta.  Every stage is flattened over the block:
+// the pairs of a level (found with two mask operations per unit) go to
+// block-wide lists -- one member present: 2 DMUL, both: 4 DMUL + 2 DADD --
+// processed by all threads, and the outputs of a round are enumerated one
+// per thread.  FP64 instructions thus run on full warps (GB300 issues FP64
+// at 2 lanes per clock per SM whatever the active mask) and no thread loops
+// over one unit's members.
+// ---------------------------------------------------------------------------
+template <int W>
+struct LocalSmem {
+    uint64_t sx[W][LB_MAX];     // x with the chunk bits cleared
+    uint64_t sz[W][LB_MAX];
+    double sc[LB_MAX];
+    double dense[LB_RU][32];
+    int32_t table[LB_TABLE];
+    unsigned occ[LB_RU];
+    int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
+    int16_t rep_uid[LB_MAX];
+    int16_t u_rep[LB_MAX];
+    uint16_t list1[LB_WARPS][LB_LIST];
+    uint16_t list2[LB_WARPS][LB_LIST];
+    uint8_t hq[LB_RU];          // qubit of the current level, per unit
+    uint8_t s_idx[LB_MAX];
+    int blk_delta[MAX_QUBITS];
+    int warp_tot[33];
+    unsigned warp_cnt[LB_WARPS];
+    unsigned long long warp_base[2][LB_WARPS];
+    long long range[2];
+    int n_units;
+};
+
+__device__ __forceinline__ unsigned level_mask(int j) {
+    // slots whose bit j is clear
+    return j == 0 ? 0x55555555u : j == 1 ? 0x33333333u : j == 2 ? 0x0f0f0f0fu : j == 3 ? 0x00ff00ffu : 0x0000ffffu;
+}
+
+// Position of the k-th set bit (0-based) of a 32-bit mask.
+__device__ __forceinline__ int nth_set_bit32(unsigned w, int k) {
+    int pos = 0;
+    int c = __popc(w & 0xffffu);
+    if (k >= c) { k -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xffu);
+    if (k >= c) { k -= c; w >>= 8; pos += 8; }
+    c = __popc(w & 0xfu);
+    if (k >= c) { k -= c; w >>= 4; pos += 4; }
+    c = __popc(w & 0x3u);
+    if (k >= c) { k -= c; w >>= 2; pos += 2; }
+    if (k >= (int)(w & 1u)) pos += 1;
+    return pos;
+}
+
+__device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, unsigned& total) {
+    const int lane = threadIdx.x & 31;
+    unsigned incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d) incl += t;
+    }
+    total = __shfl_sync(FULL_MASK, incl, 31);
+    return incl - v;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const unsigned lo = __shfl_sync(FULL_MASK, (unsigned)v, src);
+    const unsigned hi = __shfl_sync(FULL_MASK, (unsigned)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+template <int W>
+__global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
+    const void* bk, const long long* __restrict__ offsets, int n_fine, const __grid_constant__ RxRun run,
+    int pass, StrList done, StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift,
+    unsigned long long* pop_delta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LocalSmem<W>& S = *reinterpret_cast<LocalSmem<W>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(run.delta);
+
+    // ---- range: whole buckets whose start lies in [j*T, (j+1)*T)
+    if (tid < 2) {
+        const long long target = ((long long)blockIdx.x + tid) * LB_TARGET;
+        int lo = 0, hi = n_fine;  // first b in [0, n_fine] with offsets[b] >= target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (offsets[mid] >= target)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        S.range[tid] = offsets[lo];
+    }
+    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) S.blk_delta[t] = 0;
+    for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = -1;
+    __syncthreads();
+    const long long s0 = S.range[0];
+    const int m = (int)(S.range[1] - S.range[0]);
+    if (m <= 0) return;
+    if (m > LB_MAX) {
+        if (tid == 0) atomicExch(&ctr->bucket_overflow, 1u);
+        return;
+    }
+
+    // ---- load the range; key of a string = (z, x with the chunk bits cleared)
+    for (int i = tid; i < m; i += LB_THREADS) {
+        uint64_t x[W], z[W], f[W], h;
+        double c;
+        load_record<W>(bk, s0 + i, x, z, c, h);
+#pragma unroll
+        for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
+        int pos[CHUNK_BITS];
+        bool more;
+        const int np = chunk_positions<W>(f, CHUNK_BITS * pass, pos, more);
+        int idx = 0;
+        for (int j = 0; j < np; ++j) {
+            idx |= bit_of<W>(x, pos[j]) << j;
+            clear_bit<W>(x, pos[j]);
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            S.sx[w][i] = x[w];
+            S.sz[w][i] = z[w];
+        }
+        S.sc[i] = c;
+        S.s_idx[i] = (uint8_t)idx;
+        S.s_unit[i] = (int16_t)(h & (uint64_t)(LB_TABLE - 1));  // home slot, replaced below
+    }
+    __syncthreads();
+    // ---- units: shared-memory hash table on the exact key
+    for (int i = tid; i < m; i += LB_THREADS) {
+        uint64_t xb[W], z[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            xb[w] = S.sx[w][i];
+            z[w] = S.sz[w][i];
+        }
+        int slot = S.s_unit[i];
+        int rep = i;
+        for (int probe = 0; probe < LB_TABLE; ++probe) {  // 2*LB_MAX slots: never full
+            const int v = atomicCAS(&S.table[slot], -1, i);
+            if (v == -1) break;
+            bool eq = true;
+#pragma unroll
+            for (int w = 0; w < W; ++w) eq = eq && (S.sz[w][v] == z[w]) && (S.sx[w][v] == xb[w]);
+            if (eq) {
+                rep = v;
+                break;
+            }
+            slot = (slot + 1) & (LB_TABLE - 1);
+        }
+        S.s_unit[i] = (int16_t)rep;
+    }
+    __syncthreads();
+    // ---- number the units (representatives in string order)
+    constexpr int PER_T = LB_MAX / LB_THREADS;
+    {
+        int flags[PER_T], cnt = 0;
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k) {
+            const int i = tid * PER_T + k;
+            flags[k] = (i < m && S.s_unit[i] == i) ? 1 : 0;
+            cnt += flags[k];
+        }
+        int total;
+        int id = block_scan_exclusive(cnt, S.warp_tot, total);
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k) {
+            const int i = tid * PER_T + k;
+            if (flags[k]) {
+                S.rep_uid[i] = (int16_t)id;
+                S.u_rep[id] = (int16_t)i;
+                ++id;
+            }
+        }
+        if (tid == 0) S.n_units = total;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += LB_THREADS) S.s_unit[i] = S.rep_uid[S.s_unit[i]];
+    __syncthreads();
+    const int n_units = S.n_units;
+
+    // ---- rounds: warp wp owns units rbase + wp*LB_UPW + lane for lanes < LB_UPW
+    unsigned long long my_branch = 0, my_drop = 0;
+    const int ub = wp * LB_UPW;  // first unit row of this warp
+    for (int rbase = 0; rbase < n_units; rbase += LB_RU) {
+        const int u = rbase + ub + lane;
+        const bool own = lane < LB_UPW && u < n_units;
+        uint64_t z[W], xb[W], xn[W];
+        int pos[CHUNK_BITS] = {0, 0, 0, 0, 0}, pos2[CHUNK_BITS] = {0, 0, 0, 0, 0};
+        int np = 0, np2 = 0;
+        bool more = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) z[w] = xb[w] = xn[w] = 0;
+        if (own) {
+            const int rep = S.u_rep[u];
+            uint64_t f[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                z[w] = S.sz[w][rep];
+                xb[w] = S.sx[w][rep];
+                xn[w] = xb[w];
+                f[w] = z[w] & run.mask[w];
+            }
+            np = chunk_positions<W>(f, CHUNK_BITS * pass, pos, more);
+            if (more) {
+                bool m2;
+                np2 = chunk_positions<W>(f, CHUNK_BITS * (pass + 1), pos2, m2);
+                for (int j = 0; j < np2; ++j) clear_bit<W>(xn, pos2[j]);
+            }
+        }
+        if (lane < LB_UPW) S.occ[ub + lane] = 0u;
+        __syncwarp();
+        // strings of this warp's units into their slots
+        for (int i = lane; i < m; i += 32) {
+            const int ul = S.s_unit[i] - (rbase + ub);
+            if (ul >= 0 && ul < LB_UPW) {
+                const int l = S.s_idx[i];
+                S.dense[ub + ul][l] = S.sc[i];
+                atomicOr(&S.occ[ub + ul], 1u << l);
+            }
+        }
+        __syncwarp();
+        const int wnp = __reduce_max_sync(FULL_MASK, np);
+        for (int j = 0; j < wnp; ++j) {
+            const int bit = 1 << j;
+            const unsigned mj = level_mask(j);
+            const bool act = own && np > j;
+            unsigned sgl = 0, dbl = 0, hi = 0;
+            int pop_before = 0;
+            if (act) {
+                const unsigned o = S.occ[ub + lane];
+                const unsigned lo = o & mj;
+                hi = (o >> bit) & mj;
+                sgl = lo ^ hi;
+                dbl = lo & hi;
+                pop_before = __popc(o);
+                S.hq[ub + lane] = (uint8_t)pos[j];
+            }
+            unsigned tot;
+            unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
+            const unsigned n1 = tot & 0xffffu, n2 = tot >> 16;
+            unsigned o1 = o12 & 0xffffu, o2 = o12 >> 16;
+            for (unsigned b = sgl; b; b &= b - 1) {
+                const int l = __ffs(b) - 1;
+                S.list1[wp][o1++] = (uint16_t)((lane << 6) | (((hi >> l) & 1u) << 5) | l);
+            }
+            for (unsigned b = dbl; b; b &= b - 1) S.list2[wp][o2++] = (uint16_t)((lane << 5) | (__ffs(b) - 1));
+            __syncwarp();
+            for (unsigned t = lane; t < n1; t += 32) {
+                const int e = S.list1[wp][t];
+                const int ur = ub + (e >> 6), la = e & 31, lb = la | bit;
+                const bool y_side = (e & 32) != 0;
+                const int q = S.hq[ur];
+                const double v = S.dense[ur][y_side ? lb : la];
+                const double p1 = __dmul_rn(run.cs[q], v), p2 = __dmul_rn(run.sn[q], v);
+                // sigma_z present: (cos c, sin c); sigma_y present: (-sin c, cos c)
+                const double na = y_side ? __longlong_as_double(__double_as_longlong(p2) ^ (long long)0x8000000000000000ull) : p1;
+                const double nb = y_side ? p1 : p2;
+                const bool ka = keep_bits(na, dbits), kb = keep_bits(nb, dbits);
+                my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
+                S.dense[ur][la] = na;
+                S.dense[ur][lb] = nb;
+                const unsigned keep = (ka ? (1u << la) : 0u) | (kb ? (1u << lb) : 0u);
+                const unsigned drop = ((1u << la) | (1u << lb)) & ~keep;
+                if (drop) atomicAnd(&S.occ[ur], ~drop);
+                if (keep) atomicOr(&S.occ[ur], keep);
+            }
+            for (unsigned t = lane; t < n2; t += 32) {
+                const int e = S.list2[wp][t];
+                const int ur = ub + (e >> 5), la = e & 31, lb = la | bit;
+                const int q = S.hq[ur];
+                const double co = run.cs[q], sn = run.sn[q];
+                const double a = S.dense[ur][la], b = S.dense[ur][lb];
+                const double na = __dsub_rn(__dmul_rn(co, a), __dmul_rn(sn, b));
+                const double nb = __dadd_rn(__dmul_rn(co, b), __dmul_rn(sn, a));
+                const bool ka = keep_bits(na, dbits), kb = keep_bits(nb, dbits);
+                my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
+                S.dense[ur][la] = na;
+                S.dense[ur][lb] = nb;
+                const unsigned drop = (ka ? 0u : (1u << la)) | (kb ? 0u : (1u << lb));
+                if (drop) atomicAnd(&S.occ[ur], ~drop);
+            }
+            __syncwarp();
+            if (act) {
+                const int d = __popc(S.occ[ub + lane]) - pop_before;
+                my_branch += (unsigned long long)pop_before;
+                if (d) atomicAdd(&S.blk_delta[pos[j]], d);
+            }
+        }
+        // ---- outputs: flattened over the warp, one reservation per block
+        const unsigned occ = own ? S.occ[ub + lane] : 0u;
+        const unsigned nout = __popc(occ);
+        unsigned wtot;
+        const unsigned flat = warp_exclusive_scan(nout, wtot);
+        unsigned ntot;
+        const unsigned noff = warp_exclusive_scan(more ? nout : 0u, ntot);
+        if (lane == 0) S.warp_cnt[wp] = (wtot - ntot) | (ntot << 16);
+        __syncthreads();
+        if (tid < 2) {
+            unsigned long long tot = 0;
+            for (int k = 0; k < LB_WARPS; ++k) {
+                S.warp_base[tid][k] = tot;
+                const unsigned wc = S.warp_cnt[k];
+                tot += (tid == 0) ? (wc & 0xffffu) : (wc >> 16);
+            }
+            unsigned long long b = 0;
+            if (tot) b = atomicAdd(tid == 0 ? &ctr->n_done : &ctr->n_next, tot);
+            for (int k = 0; k < LB_WARPS; ++k) S.warp_base[tid][k] += b;
+        }
+        __syncthreads();
+        const unsigned long long base_done = S.warp_base[0][wp], base_next = S.warp_base[1][wp];
+        const unsigned doff = flat - noff;  // done-list offset of this lane's unit
+        for (unsigned kb = 0; kb < wtot; kb += 32) {
+            const unsigned k = kb + lane;
+            // owner lane: last L < LB_UPW with flat(L) <= k
+            int lo = 0, hi2 = LB_UPW - 1;
+#pragma unroll
+            for (int step = 0; step < 4; ++step) {
+                const int mid = (lo + hi2 + 1) >> 1;
+                const unsigned fm = __shfl_sync(FULL_MASK, flat, mid);
+                if (fm <= k)
+                    lo = mid;
+                else
+                    hi2 = mid - 1;
+            }
+            const int L = lo;
+            const unsigned oc = __shfl_sync(FULL_MASK, occ, L);
+            const unsigned fl = __shfl_sync(FULL_MASK, flat, L);
+            const bool mr = __shfl_sync(FULL_MASK, (int)more, L) != 0;
+            const unsigned dof = __shfl_sync(FULL_MASK, doff, L);
+            const unsigned nof = __shfl_sync(FULL_MASK, noff, L);
+            const int npl = __shfl_sync(FULL_MASK, np, L);
+            const int np2l = __shfl_sync(FULL_MASK, np2, L);
+            uint64_t x[W], zz[W], x2[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                x[w] = shfl64(xb[w], L);
+                zz[w] = shfl64(z[w], L);
+                x2[w] = shfl64(xn[w], L);
+            }
+            int pl[CHUNK_BITS], p2l[CHUNK_BITS];
+#pragma unroll
+            for (int j = 0; j < CHUNK_BITS; ++j) {
+                pl[j] = __shfl_sync(FULL_MASK, pos[j], L);
+                p2l[j] = __shfl_sync(FULL_MASK, pos2[j], L);
+            }
+            if (k >= wtot) continue;
+            const int r = (int)(k - fl);
+            const int l = nth_set_bit32(oc, r);
+            for (int j = 0; j < npl; ++j)
+                if ((l >> j) & 1) {
+                    set_bit<W>(x, pl[j]);
+                    set_bit<W>(x2, pl[j]);
+                }
+            const long long slot = (long long)(mr ? base_next + nof + r : base_done + dof + r);
+            StrList dst = mr ? next : done;
+            uint64_t h = 0;
+            if (mr) {
+                // the next pass's chunk bits are cleared in its key (some of them
+                // may be this pass's bits just set)
+                for (int j = 0; j < np2l; ++j) clear_bit<W>(x2, p2l[j]);
+                h = hash_key<W>(zz, x2);
+                atomicAdd(&fcount_next[fine_bucket(h, fshift)], 1);
+            }
+            if (slot < cap) {
+                store_plane<W>(dst.x, slot, x);
+                store_plane<W>(dst.z, slot, zz);
+                dst.c[slot] = S.dense[ub + L][l];
+                if (mr) dst.h[slot] = h;
+            } else {
+                ctr->overflow = 1u;
+            }
+        }
+        __syncwarp();
+    }
+    const unsigned nb = __reduce_add_sync(FULL_MASK, (unsigned)my_branch);
+    const unsigned nd = __reduce_add_sync(FULL_MASK, (unsigned)my_drop);
+    if (lane == 0 && (nb | nd)) {
+        atomicAdd(&ctr->branch_events, (unsigned long long)nb);
+        atomicAdd(&ctr->dropped, (unsigned long long)nd);
+    }
+    __syncthreads();
+    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)
+        if (S.blk_delta[t]) atomicAdd(&pop_delta[t], (unsigned long long)(long long)S.blk_delta[t]);
+}
+
+}  // namespace orqa
