@@ -31,7 +31,9 @@ sys.path.insert(0, ROOT)
 
 from paper_2506_13241_gb300 import workloads as W  # noqa: E402
 
-DEFAULT_WORKLOAD = "heavyhex"
+# 127-qubit heavy-hex kicked Ising, theta_x = pi/4, 20 steps, delta chosen so
+# that the live set peaks near 1e9 strings
+DEFAULT_WORKLOAD = "heavyhex_t=20_delta=3.5e-6"
 METRIC = "Pauli string-gate updates/s"
 UNIT = "string-gate updates/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -40,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="orqa", choices=["orqa", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -60,8 +62,15 @@ def measured_peaks():
 
 
 def default_capacity(wl):
-    # strings per buffer; the workspace is ~230 B per unit of capacity at W=2
-    return {"heavyhex": 1 << 21}.get(wl["name"], int(4e8))
+    """Strings per buffer (the workspace is ~196 B per unit of capacity at
+    127 qubits).  Peaks measured for theta_x = pi/4 over 20 steps: 2.3e6 at
+    delta = 1e-4, 2.0e7 at 3e-5, 1.5e8 at 1e-5, 5.5e8 at 5e-6; they grow
+    about as delta^-1.8."""
+    d = wl["delta"]
+    if d <= 0.0:
+        return int(2.5e7)
+    est = 5.5e8 * (5e-6 / d) ** 1.8
+    return int(min(max(1.35 * est, 1 << 21), 1.3e9))
 
 
 # ---------------------------------------------------------------------------
@@ -144,6 +153,8 @@ def make_gpu_runner(wl, capacity, profile=True):
     c_p = torch.from_numpy(c_h).pin_memory()
     delta = wl["delta"]
 
+    fp64 = {"one": 0, "two": 0}
+
     def evolve():
         updates, mags, peak = 0, [], 0
         for _ in range(wl["steps"]):
@@ -152,6 +163,8 @@ def make_gpu_runner(wl, capacity, profile=True):
                 s = B.orqa_stats(ctx.ctx)
                 updates += s["string_gate_updates"]
                 peak = max(peak, s["last_layer_peak"])
+                fp64["one"] += s["pair_updates_one"]
+                fp64["two"] += s["pair_updates_two"]
             mags.append(B.orqa_expect(ctx.ctx))
         return updates, mags, peak
 
@@ -166,7 +179,7 @@ def make_gpu_runner(wl, capacity, profile=True):
 
     h2d = x_h.nbytes + z_h.nbytes + c_h.nbytes
     d2h = 8 * wl["steps"]
-    return ctx, step_device, step_host, h2d, d2h
+    return ctx, step_device, step_host, h2d, d2h, fp64
 
 
 def run_gpu(args, wl, rank, world):
@@ -174,7 +187,7 @@ def run_gpu(args, wl, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     capacity = int(args.capacity) if args.capacity else default_capacity(wl)
-    ctx, step_dev, step_host, h2d, d2h = make_gpu_runner(wl, capacity)
+    ctx, step_dev, step_host, h2d, d2h, fp64 = make_gpu_runner(wl, capacity)
     stream = ctx.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -187,6 +200,7 @@ def run_gpu(args, wl, rank, world):
         step_dev()
     torch.cuda.synchronize()
     ctx.profile_reset()
+    fp64["one"] = fp64["two"] = 0
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -208,9 +222,10 @@ def run_gpu(args, wl, rank, world):
     barrier()
     clk = clocks.stop()
     prof = ctx.profile()
+    fp64_ops = 2 * fp64["one"] + 6 * fp64["two"]
     # end to end through the public API with host buffers
     e2e_s, e2e_updates = 0.0, 0
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, min(args.steps, 2))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -226,7 +241,22 @@ def run_gpu(args, wl, rank, world):
         times = t.tolist()
     return dict(total_ms=times[0], updates=total_updates, mags=mags, peak=peak, clocks=clk,
                 prof=prof, e2e_s=times[1], e2e_updates=e2e_updates, h2d=h2d, d2h=d2h,
-                capacity=capacity)
+                capacity=capacity, fp64_ops=fp64_ops)
+
+
+def fp64_entry(prof, fp64_ops, sm_mhz):
+    """FP64 view of the unit kernel: the pair updates need 2 (one member) or
+    6 (both) FP64 operations; GB300 issues FP64 at 2 lanes per clock per SM."""
+    local = [p for p in prof if p["name"] == "unit_local" and p["ms"] > 0]
+    if not local:
+        return None
+    ms = local[0]["ms"]
+    mhz = sm_mhz or 2070.0
+    peak = 2.0 * 152 * mhz * 1e6
+    achieved = fp64_ops / (ms * 1e-3)
+    return {"kernel": "unit_local", "ops": fp64_ops, "achieved_ops_per_s": achieved,
+            "peak_ops_per_s": peak, "frac": round(achieved / peak, 4),
+            "peak_note": "2 FP64 lanes/clock/SM x 152 SMs x median SM clock (ncu peak_sustained)"}
 
 
 def roofline_entry(prof, steps):
@@ -251,46 +281,56 @@ def roofline_entry(prof, steps):
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
+ORACLE_MAX_TERMS = 20_000_000  # keeps the std::map oracle within a few GB of host memory
+
+
 def oracle_sample(wl, seconds: float):
-    """Runs the oracle on the workload's first time steps, gate by gate,
-    until about ``seconds`` have passed; returns updates, time, steps."""
+    """Runs the oracle on the workload from its start, gate by gate, and stops
+    after the gate that passes ``seconds`` (or when the operator outgrows
+    ORACLE_MAX_TERMS), so the sample is bounded whatever the workload size.
+    Returns (updates, seconds used, whole time steps done, gates done in the
+    last partial step, <M_t> of the whole steps)."""
     import oracle
     n = wl["n"]
     op = oracle.Oracle(n)
     for lab, c in wl["observable"]:
         op.add_label(lab, c)
-    updates, t_used, steps = 0, 0.0, 0
+    updates, t_used, steps, mags, partial = 0, 0.0, 0, [], 0
+    t0 = time.perf_counter()
     for t in range(wl["steps"]):
-        t0 = time.perf_counter()
+        partial = 0
         for layer in wl["layers"]:
             for g in layer:
-                updates += len(op)
+                size = len(op)
+                if time.perf_counter() - t0 >= seconds or size > ORACLE_MAX_TERMS:
+                    return updates, time.perf_counter() - t0, steps, partial, mags
+                updates += size
                 op.apply(g, wl["delta"])
-        op.expect_zero()
-        t_used += time.perf_counter() - t0
+                partial += 1
+        mags.append(op.expect_zero())
         steps = t + 1
-        if t_used >= seconds:
-            break
-    return updates, t_used, steps
+    return updates, time.perf_counter() - t0, steps, 0, mags
 
 
 def cpu_baseline(wl, seconds):
-    upd, secs, steps = oracle_sample(wl, seconds)
+    upd, secs, steps, partial, mags = oracle_sample(wl, seconds)
     return {"value": upd / secs if secs > 0 else None, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d of %d time steps of %s (%d string-gate updates, %.1f s)" % (
-                steps, wl["steps"], wl["name"], upd, secs)}
+            "sample": "first %d of %d time steps of %s plus %d gates of the next (%d string-gate "
+                      "updates, %.1f s)" % (steps, wl["steps"], wl["name"], partial, upd, secs),
+            "magnetization": mags}
 
 
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    seconds = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    seconds = min(20.0, max(2.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(wl, seconds)
     upd, secs, steps = 0, 0.0, 0
+    partial = 0
     for _ in range(args.steps):
-        u, s, st = oracle_sample(wl, seconds)
+        u, s, st, partial, _ = oracle_sample(wl, seconds)
         upd += u
         secs += s
         steps = st
@@ -301,8 +341,8 @@ def run_reference(args, wl):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "first %d of %d time steps of %s per step" % (
-                                 steps, wl["steps"], wl["name"])},
+                             "sample": "first %d of %d time steps of %s plus %d gates, per step" % (
+                                 steps, wl["steps"], wl["name"], partial)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -355,8 +395,14 @@ def main(argv=None):
                     "d2h_bytes_per_step": res["d2h"]},
             "gpu_launches": launches, "clocks": res["clocks"],
             "magnetization": res["mags"], "peak_strings": res["peak"], "capacity": res["capacity"]}
+    line["fp64"] = fp64_entry(res["prof"], res["fp64_ops"], res["clocks"].get("sm_mhz"))
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        cb = cpu_baseline(wl, args.cpu_seconds)
+        om = cb.pop("magnetization")
+        k = min(len(om), len(res["mags"]))
+        line["magnetization_error_vs_oracle"] = {
+            "steps_compared": k, "max_abs": max(abs(a - b) for a, b in zip(res["mags"][:k], om[:k]))}
+        line["cpu_baseline"] = cb
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -90,6 +90,8 @@ typedef struct {
     int64_t string_gate_updates; /* sum over its gates of |O| before the gate */
     int64_t branch_events;    /* anticommuting (string, gate) pairs in it */
     int64_t dropped;          /* strings removed by truncation in it */
+    int64_t pair_updates_one; /* (pair, gate) updates with one member present */
+    int64_t pair_updates_two; /* (pair, gate) updates with both members present */
     int32_t chunk_passes;     /* device passes its rotation layer took */
     int32_t pad;
 } orqa_stats_t;

@@ -3,6 +3,7 @@
 // workspace, computes cos/sin of each gate once, launches kernels on the
 // caller's stream and reads back small counters; every per-string step runs
 // on the device.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -59,9 +60,9 @@ struct orqa_ctx {
     int fshift = 0;
     int32_t* fcount[2] = {nullptr, nullptr};
     long long* foffsets = nullptr;
-    long long* fcursor = nullptr;
     long long* tile_sums = nullptr;
     uint64_t* hash_active = nullptr;   // unit-key hashes of the active list
+    int32_t* rank_active = nullptr;    // ranks inside their fine buckets
     void* records = nullptr;           // bucket-ordered copy of the active list
     size_t local_smem = 0;
     Counters* ctr = nullptr;
@@ -104,43 +105,51 @@ long long pow2_at_least(long long v) {
 
 struct Layout {
     size_t str_x, str_c;  // per string buffer: x and z planes, c
+    size_t shared;        // region shared by the layer scratch and the merge scratch
     size_t total;
-    long long table_cap;
+    long long table_cap;  // merge hash table slots
     long long n_fine;
 };
 
-// Fine buckets: about 32 strings each at full capacity, a power of two and a
+// Fine buckets: about 16 strings each at full capacity, a power of two and a
 // multiple of the scan tile, at most SCAN_TILE tiles.
 long long fine_buckets(long long cap) {
     long long f = SCAN_TILE;
-    while (f < cap / 32 && f < (long long)SCAN_TILE * SCAN_TILE) f <<= 1;
+    while (f < cap / 16 && f < (long long)SCAN_TILE * SCAN_TILE) f <<= 1;
     return f;
 }
 
-// Offsets are computed in the same order by workspace_bytes and carve().
+// The X-layer scratch (bucket records, hashes and ranks of the active list)
+// and the duplicate-merge scratch (entry tables, coefficients, hash table)
+// are never live at the same time, so they share one region.
+size_t layer_scratch_bytes(int W, size_t C) {
+    return align_up(C * (size_t)record_bytes(W)) + align_up(C * 8) + align_up(C * 4);
+}
+
+size_t merge_scratch_bytes(int W, size_t C, long long table_cap) {
+    return 2 * align_up(C * 4) + 2 * align_up(C * W * 8) + align_up(C * 4) + 2 * align_up(C * 8) +
+           align_up((size_t)table_cap * 4);
+}
+
+// Offsets are computed in the same order by orqa_workspace_bytes and
+// orqa_create.
 Layout layout(int n_qubits, long long cap) {
     Layout L{};
     const int W = n_qubits <= 64 ? 1 : 2;
     const size_t C = (size_t)cap;
     L.str_x = align_up(C * W * 8);
     L.str_c = align_up(C * 8);
-    L.table_cap = pow2_at_least(2 * cap);
+    // merge table at load factor <= 0.75; the shared region covers both uses
+    L.table_cap = pow2_at_least((4 * cap + 2) / 3);
+    L.shared = std::max(layer_scratch_bytes(W, C), merge_scratch_bytes(W, C, L.table_cap));
     L.n_fine = fine_buckets(cap);
     const size_t F = (size_t)L.n_fine;
     size_t t = 0;
     t += 3 * (2 * L.str_x + L.str_c);     // three string buffers
-    t += 2 * align_up(C * 4);              // uid, rank
-    t += 2 * L.str_x;                      // unit_z, unit_xb
-    t += align_up(C * 4);                  // unit_count
-    t += align_up(C * 8);                  // unit_off
-    t += align_up(C * 8);                  // sorted_c
-    t += align_up((size_t)L.table_cap * 4);  // hash table
+    t += L.shared;                         // layer / merge scratch
     t += 2 * align_up(F * 4);              // fine counts (two passes)
     t += align_up((F + 1) * 8);            // fine offsets
-    t += align_up(F * 8);                  // fine cursors
     t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
-    t += align_up(C * 8);                  // unit-key hashes of the active list
-    t += align_up(C * (size_t)record_bytes(W));  // bucket records
     t += align_up(sizeof(Counters));
     t += align_up(MAX_QUBITS * 8);
     t += align_up(EXPECT_BLOCKS * 8);
@@ -265,8 +274,8 @@ orqa_status check_flags(orqa_ctx* ctx, const Counters& h, const char* what) {
 template <int W>
 orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, double delta,
                        long long* n_out) {
-    const long long tcap = pow2_at_least(2 * (n > 0 ? n : 1));
-    if (tcap > ctx->table_cap) return fail(ctx, ORQA_ECAPACITY, "merge: hash table too small");
+    const long long tcap = std::min(pow2_at_least(2 * (n > 0 ? n : 1)), ctx->table_cap);
+    if (4 * n > 3 * tcap) return fail(ctx, ORQA_ECAPACITY, "merge: hash table too small");
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     int r_as = -1, r_off = -1, r_sc = -1, r_red = -1;
     if (n > 0) {
@@ -308,10 +317,14 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
     return ORQA_OK;
 }
 
-template <int W>
-orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
-    std::vector<ZZLayer> launches;
-    ZZLayer L{};
+// Groups the edges of a ZZ layer for k_rzz_layer: one set per Clifford mode
+// (a repeated edge opens a new set), each set split by offset d = j - i into
+// masks of left endpoints.  Launches are cut at MAX_ZZ_SETS / MAX_ZZ_GROUPS;
+// all gates commute, so any such order is the array order's result.
+orqa_status build_zz_groups(orqa_ctx* ctx, const orqa_gate* g, int ng, std::vector<ZZGroups>& launches) {
+    struct Edge { int i, j, mode; };
+    std::vector<std::vector<Edge>> sets;   // edges per set
+    std::vector<int> set_mode;
     for (int k = 0; k < ng; ++k) {
         double c, s;
         bool cl;
@@ -323,18 +336,54 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         else
             mode = (s < 0) ? 2 : 3;
         if (mode == 0) continue;
-        if (L.n_edges == MAX_EDGES) {
-            launches.push_back(L);
-            L = ZZLayer{};
+        const int i = std::min(g[k].q0, g[k].q1), j = std::max(g[k].q0, g[k].q1);
+        int target = -1;
+        for (int t = 0; t < (int)sets.size() && target < 0; ++t) {
+            if (set_mode[t] != mode) continue;
+            bool dup = false;
+            for (const Edge& e : sets[t]) dup = dup || (e.i == i && e.j == j);
+            if (!dup) target = t;
         }
-        L.qi[L.n_edges] = (uint8_t)g[k].q0;
-        L.qj[L.n_edges] = (uint8_t)g[k].q1;
-        L.mode[L.n_edges] = (uint8_t)mode;
-        ++L.n_edges;
+        if (target < 0) {
+            sets.push_back({});
+            set_mode.push_back(mode);
+            target = (int)sets.size() - 1;
+        }
+        sets[target].push_back({i, j, mode});
     }
-    if (L.n_edges) launches.push_back(L);
+    ZZGroups cur{};
+    for (size_t t = 0; t < sets.size(); ++t) {
+        // offset groups of this set
+        std::vector<int> ds;
+        for (const Edge& e : sets[t])
+            if (std::find(ds.begin(), ds.end(), e.j - e.i) == ds.end()) ds.push_back(e.j - e.i);
+        std::sort(ds.begin(), ds.end());
+        if (cur.n_sets == MAX_ZZ_SETS || cur.n_groups + (int)ds.size() > MAX_ZZ_GROUPS) {
+            launches.push_back(cur);
+            cur = ZZGroups{};
+        }
+        for (int d : ds) {
+            const int gi = cur.n_groups++;
+            cur.d[gi] = d;
+            cur.mask[gi][0] = cur.mask[gi][1] = 0;
+            for (const Edge& e : sets[t])
+                if (e.j - e.i == d) cur.mask[gi][e.i >> 6] |= 1ull << (e.i & 63);
+        }
+        cur.set_mode[cur.n_sets] = set_mode[t];
+        cur.set_end[cur.n_sets] = cur.n_groups;
+        ++cur.n_sets;
+    }
+    if (cur.n_sets) launches.push_back(cur);
+    return ORQA_OK;
+}
+
+template <int W>
+orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
+    std::vector<ZZGroups> launches;
+    orqa_status bst = build_zz_groups(ctx, g, ng, launches);
+    if (bst != ORQA_OK) return bst;
     StrList s = ctx->buf[ctx->cur];
-    for (const ZZLayer& l : launches) {
+    for (const ZZGroups& l : launches) {
         if (ctx->n == 0) break;
         const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (8.0 * (2 * W + 1) + 8.0 * W + 8.0));
         k_rzz_layer<W><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, l);
@@ -346,6 +395,8 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     ctx->stats.string_gate_updates = (int64_t)ctx->n * ng;
     ctx->stats.branch_events = 0;
     ctx->stats.dropped = 0;
+    ctx->stats.pair_updates_one = 0;
+    ctx->stats.pair_updates_two = 0;
     ctx->stats.chunk_passes = 0;
     if (delta > ctx->clean_delta && ctx->n > 0) {
         const int dst = (ctx->cur + 1) % 3;
@@ -369,13 +420,13 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     return ORQA_OK;
 }
 
-// Exclusive scan of fine-bucket counts fcount[k] into foffsets / fcursor.
+// Exclusive scan of fine-bucket counts fcount[k] into foffsets.
 orqa_status fine_scan(orqa_ctx* ctx, int k) {
     const int tiles = ctx->n_fine / SCAN_TILE;
-    const int r = prof_begin(ctx, K_SCAN, (double)ctx->n_fine * 28.0);
+    const int r = prof_begin(ctx, K_SCAN, (double)ctx->n_fine * 20.0);
     k_scan_tiles<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->fcount[k], ctx->foffsets, ctx->tile_sums);
     k_scan_top<<<1, SCAN_THREADS, 0, ctx->stream>>>(ctx->tile_sums, tiles);
-    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->fcursor, ctx->tile_sums, ctx->n_fine);
+    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->tile_sums, ctx->n_fine);
     prof_end(ctx, r);
     LAUNCH_CHECK(ctx);
     return ORQA_OK;
@@ -399,6 +450,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     const int D = (S + 1) % 3;
     StrList act = ctx->buf[(S + 2) % 3];
     act.h = ctx->hash_active;
+    act.rank = ctx->rank_active;
     const long long n_in = ctx->n;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
@@ -429,9 +481,9 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount[fc ^ 1], 0, (size_t)ctx->n_fine * 4, ctx->stream));
         CUDA_TRY(ctx, cudaMemsetAsync(&ctx->ctr->n_next, 0, sizeof(unsigned long long), ctx->stream));
         const unsigned long long done_before = h.n_done;
-        const int r_sc = prof_begin(ctx, K_BUCKET_SCATTER, (double)n_active * (R + 8.0 + record_bytes(W)));
+        const int r_sc = prof_begin(ctx, K_BUCKET_SCATTER, (double)n_active * (R + 12.0 + record_bytes(W)));
         k_bucket_scatter<W><<<grid_for(ctx, (n_active + SCATTER_ILP - 1) / SCATTER_ILP), 256, 0, ctx->stream>>>(
-            act, n_active, ctx->fshift, ctx->fcursor, ctx->records);
+            act, n_active, ctx->fshift, ctx->foffsets, ctx->records);
         prof_end(ctx, r_sc);
         LAUNCH_CHECK(ctx);
         const long long ranges = (n_active + LB_TARGET - 1) / LB_TARGET;
@@ -474,6 +526,8 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     ctx->stats.string_gate_updates = updates;
     ctx->stats.branch_events = (int64_t)h.branch_events;
     ctx->stats.dropped = (int64_t)h.dropped;
+    ctx->stats.pair_updates_one = (int64_t)h.pairs_one;
+    ctx->stats.pair_updates_two = (int64_t)h.pairs_two;
     ctx->stats.chunk_passes = pass;
     return ORQA_OK;
 }
@@ -552,26 +606,33 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
         ctx->buf[b].z = (uint64_t*)p; p += L.str_x;
         ctx->buf[b].c = (double*)p;   p += L.str_c;
         ctx->buf[b].h = nullptr;
+        ctx->buf[b].rank = nullptr;
     }
-    ctx->uid = (int32_t*)p; p += align_up(C * 4);
-    ctx->rank = (int32_t*)p; p += align_up(C * 4);
-    ctx->unit_z = (uint64_t*)p; p += L.str_x;
-    ctx->unit_xb = (uint64_t*)p; p += L.str_x;
-    ctx->unit_count = (int32_t*)p; p += align_up(C * 4);
-    ctx->unit_off = (long long*)p; p += align_up(C * 8);
-    ctx->sorted_c = (double*)p; p += align_up(C * 8);
-    ctx->table = (int32_t*)p; p += align_up((size_t)L.table_cap * 4);
-    ctx->table_cap = L.table_cap;
+    {
+        // layer scratch and merge scratch: two views of one region
+        char* q = p;
+        ctx->records = (void*)q; q += align_up(C * (size_t)record_bytes(ctx->W));
+        ctx->hash_active = (uint64_t*)q; q += align_up(C * 8);
+        ctx->rank_active = (int32_t*)q;
+        q = p;
+        ctx->uid = (int32_t*)q; q += align_up(C * 4);
+        ctx->rank = (int32_t*)q; q += align_up(C * 4);
+        ctx->unit_z = (uint64_t*)q; q += align_up(C * ctx->W * 8);
+        ctx->unit_xb = (uint64_t*)q; q += align_up(C * ctx->W * 8);
+        ctx->unit_count = (int32_t*)q; q += align_up(C * 4);
+        ctx->unit_off = (long long*)q; q += align_up(C * 8);
+        ctx->sorted_c = (double*)q; q += align_up(C * 8);
+        ctx->table = (int32_t*)q;
+        ctx->table_cap = L.table_cap;
+        p += L.shared;
+    }
     const size_t F = (size_t)L.n_fine;
     ctx->n_fine = (int)L.n_fine;
     ctx->fshift = 64 - __builtin_ctzll((unsigned long long)L.n_fine);
     ctx->fcount[0] = (int32_t*)p; p += align_up(F * 4);
     ctx->fcount[1] = (int32_t*)p; p += align_up(F * 4);
     ctx->foffsets = (long long*)p; p += align_up((F + 1) * 8);
-    ctx->fcursor = (long long*)p; p += align_up(F * 8);
     ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
-    ctx->hash_active = (uint64_t*)p; p += align_up(C * 8);
-    ctx->records = (void*)p; p += align_up(C * (size_t)record_bytes(ctx->W));
     ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));
     ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
     ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);

@@ -10,7 +10,6 @@ namespace orqa {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr int MAX_QUBITS = 128;
-constexpr int MAX_EDGES = 1024;   // ZZ gates per kernel launch
 constexpr int CHUNK_BITS = 5;     // rotation qubits per unit pass: 2^5 = one warp
 constexpr int32_t SLOT_EMPTY = -1;
 constexpr int32_t SLOT_BUSY = -2;
@@ -23,7 +22,8 @@ struct StrList {
     uint64_t* x;
     uint64_t* z;
     double* c;
-    uint64_t* h;  // per-string unit-key hash for the next chunk pass (layer lists only)
+    uint64_t* h;     // per-string unit-key hash for the next chunk pass (active list only)
+    int32_t* rank;   // per-string rank inside its fine bucket (active list only)
 };
 
 // Device counters shared by the kernels of one call.
@@ -34,6 +34,8 @@ struct Counters {
     unsigned long long unit_cursor;  // next free element slot for unit offsets
     unsigned long long branch_events;
     unsigned long long dropped;
+    unsigned long long pairs_one;    // pair updates with one member present (2 DMUL)
+    unsigned long long pairs_two;    // pair updates with both present (4 DMUL + 2 DADD)
     unsigned int overflow;           // an append would have exceeded capacity
     unsigned int timeout;            // a bounded spin-wait gave up
     unsigned int table_full;         // the hash table had no free slot
@@ -51,17 +53,23 @@ struct RxRun {
     double sn[MAX_QUBITS];   // sin(theta_q)
 };
 
-// ZZ layer parameters: one mode per edge.
+// ZZ layer parameters.  Edges of one Clifford mode form a set; a set is
+// stored as offset groups: the edges (i, i + d) of the set, as the mask of
+// their left endpoints i.  Sets are applied in order.
 //   mode 1: (cos, sin) = (-1, 0)  anticommuting strings change sign
 //   mode 2: (cos, sin) = ( 0,-1)  z_i, z_j flip; sign flips iff the
 //                                  anticommuting site was Y
 //   mode 3: (cos, sin) = ( 0,+1)  z_i, z_j flip; sign flips iff it was X
-struct ZZLayer {
-    int32_t n_edges;
-    int32_t pad;
-    uint8_t qi[MAX_EDGES];
-    uint8_t qj[MAX_EDGES];
-    uint8_t mode[MAX_EDGES];
+constexpr int MAX_ZZ_GROUPS = 256;
+constexpr int MAX_ZZ_SETS = 32;
+
+struct ZZGroups {
+    int32_t n_sets;
+    int32_t n_groups;
+    int32_t set_mode[MAX_ZZ_SETS];
+    int32_t set_end[MAX_ZZ_SETS];    // one past the set's last group
+    int32_t d[MAX_ZZ_GROUPS];
+    uint64_t mask[MAX_ZZ_GROUPS][2];
 };
 
 template <int W>
@@ -102,6 +110,37 @@ __device__ __forceinline__ int get_bit(const uint64_t* v, int q) {
 
 // Register-only bit access for W-word planes (no dynamic array indexing, so
 // the planes stay in registers).
+// v >> d and v << d on W-word planes, 0 < d < 64 W.
+template <int W>
+__device__ __forceinline__ void shr_planes(const uint64_t (&v)[W], int d, uint64_t (&r)[W]) {
+    if constexpr (W == 1) {
+        r[0] = v[0] >> d;
+    } else {
+        if (d >= 64) {
+            r[0] = v[1] >> (d - 64);
+            r[1] = 0;
+        } else {
+            r[0] = (v[0] >> d) | (v[1] << (64 - d));
+            r[1] = v[1] >> d;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void shl_planes(const uint64_t (&v)[W], int d, uint64_t (&r)[W]) {
+    if constexpr (W == 1) {
+        r[0] = v[0] << d;
+    } else {
+        if (d >= 64) {
+            r[1] = v[0] << (d - 64);
+            r[0] = 0;
+        } else {
+            r[1] = (v[1] << d) | (v[0] >> (64 - d));
+            r[0] = v[0] << d;
+        }
+    }
+}
+
 template <int W>
 __device__ __forceinline__ int bit_of(const uint64_t (&v)[W], int q) {
     if constexpr (W == 1) {

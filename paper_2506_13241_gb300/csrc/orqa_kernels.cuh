@@ -12,35 +12,74 @@ namespace orqa {
 // ---------------------------------------------------------------------------
 // ZZ layer (Clifford).  Conjugation by exp(-i theta/2 Z_i Z_j) at theta a
 // multiple of pi/2 (Eq. eq:u with theta_zz = -pi/2; Eq. update_rule with
-// cos in {0, +-1}).  A string anticommutes with Z_i Z_j iff x_i xor x_j = 1.
-// For cos = 0 its image is the single string with z_i, z_j flipped and
-// coefficient (-1)^((B+1)/2) sin(theta) c; working out B(I, Z_i Z_j) for the
-// anticommuting site gives: for sin = -1 the sign flips iff that site was Y
-// (x = z = 1) before the gate, for sin = +1 iff it was X.  Edges are applied
-// in array order, each seeing the planes left by the previous ones.  In
-// place: one read and one write of z and c per string.
+// cos in {0, +-1}).  A string anticommutes with Z_i Z_j iff x_i xor x_j = 1;
+// for cos = 0 its image is the single string with z_i, z_j flipped and
+// coefficient (-1)^((B+1)/2) sin(theta) c, which for sin = -1 flips the sign
+// iff the anticommuting site (the endpoint with x = 1) is Y before the gate.
+//
+// All gates of a set commute, so the set is applied in closed form.  Let
+// n_s be the number of anticommuting edges at site s (neighbours t with
+// x_t != x_s) and C0, C1 the planes of its bits 0 and 1.  Every such edge
+// flips z_s, so z' = z xor C0.  Taking the edges in any order, the sign
+// flips once per edge whose x = 1 endpoint s has odd z_s at that moment:
+// z_s(original) summed over the n_s edges at s, plus one flip per pair of
+// edges at s (the earlier one flips z_s for the later one), i.e.
+//   sign(sin = -1) = parity(x & ((z & C0) ^ C1)),
+//   sign(sin = +1) = parity(x & ((z & C0) ^ C1 ^ C0))   (flip iff X),
+//   sign(cos = -1) = parity(x & C0)                      (one per edge).
+// C0, C1 come from offset groups: the anticommuting edges (i, i + d) of a
+// group are a = (x ^ (x >> d)) & mask, counted at i (a) and at i + d
+// (a << d) by a 2-bit carry-save counter.  In place: one read of x, z, c and
+// one write of z, c per string.
 // ---------------------------------------------------------------------------
 template <int W>
-__global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n,
-                                                   const __grid_constant__ ZZLayer L) {
+__global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n, const __grid_constant__ ZZGroups G) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint64_t x[W], z[W];
         load_plane<W>(s.x, i, x);
         load_plane<W>(s.z, i, z);
         unsigned neg = 0;
-        for (int e = 0; e < L.n_edges; ++e) {
-            const int qi = L.qi[e], qj = L.qj[e], mode = L.mode[e];
-            const int xi = get_bit(x, qi), xj = get_bit(x, qj);
-            if ((xi ^ xj) == 0) continue;
-            if (mode == 1) {
-                neg ^= 1u;
-                continue;
+        int g = 0;
+        for (int k = 0; k < G.n_sets; ++k) {
+            uint64_t c0[W], c1[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) c0[w] = c1[w] = 0;
+            for (; g < G.set_end[k]; ++g) {
+                const int d = G.d[g];
+                uint64_t sh[W], a[W], b[W];
+                shr_planes<W>(x, d, sh);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    a[w] = (x[w] ^ sh[w]) & G.mask[g][w];
+                    c1[w] ^= c0[w] & a[w];
+                    c0[w] ^= a[w];
+                }
+                shl_planes<W>(a, d, b);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    c1[w] ^= c0[w] & b[w];
+                    c0[w] ^= b[w];
+                }
             }
-            const int zsrc = xi ? get_bit(z, qi) : get_bit(z, qj);
-            neg ^= (mode == 2) ? (unsigned)zsrc : (unsigned)(zsrc ^ 1);
-            z[qi >> 6] ^= 1ull << (qi & 63);
-            z[qj >> 6] ^= 1ull << (qj & 63);
+            const int mode = G.set_mode[k];
+            unsigned par = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint64_t t;
+                if (mode == 1)
+                    t = x[w] & c0[w];
+                else if (mode == 2)
+                    t = x[w] & ((z[w] & c0[w]) ^ c1[w]);
+                else
+                    t = x[w] & ((z[w] & c0[w]) ^ c1[w] ^ c0[w]);
+                par ^= (unsigned)__popcll(t);
+            }
+            neg ^= par & 1u;
+            if (mode != 1) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) z[w] ^= c0[w];
+            }
         }
         store_plane<W>(s.z, i, z);
         if (neg) s.c[i] = -s.c[i];

@@ -36,7 +36,7 @@ constexpr int LB_UPW = 16;          // units a warp owns per round (lanes 0..15)
 constexpr int LB_RU = LB_WARPS * LB_UPW;  // units per round
 constexpr int LB_LIST = LB_UPW * 16;      // most pairs of one level in a warp
 constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int)(h >> fshift); }
@@ -93,8 +93,11 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrL
                 int pos[CHUNK_BITS], np, idx;
                 bool more;
                 const uint64_t h = unit_key_hash<W>(x, z, run.mask, 0, pos, np, idx, more);
-                if (slot < cap) active.h[slot] = h;
-                atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
+                const int rk = atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
+                if (slot < cap) {
+                    active.h[slot] = h;
+                    active.rank[slot] = rk;
+                }
             }
         }
         const unsigned nd = __popc(__ballot_sync(FULL_MASK, live && !act && !keep));
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrL
 // ---------------------------------------------------------------------------
 // Exclusive scan of the fine-bucket counts (n = number of buckets, a
 // multiple of SCAN_TILE): tile sums, a one-block scan of the tile sums,
-// then offsets[b] and cursor[b] = offsets[b]; offsets[n] = total.
+// then offsets[b]; offsets[n] = total.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& total) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -179,26 +182,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums,
     if (t == 0) tile_sums[SCAN_TILE] = total;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, long long* cursor,
-                                                           const long long* tile_sums, long long n) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, const long long* tile_sums,
+                                                           long long n) {
     const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
     const long long add = tile_sums[blockIdx.x];
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        const long long o = offsets[base + k] + add;
-        offsets[base + k] = o;
-        cursor[base + k] = o;
-    }
+    for (int k = 0; k < SCAN_ITEMS; ++k) offsets[base + k] += add;
     if (blockIdx.x == 0 && threadIdx.x == 0) offsets[n] = tile_sums[SCAN_TILE];
 }
 
 // ---------------------------------------------------------------------------
 // Scatter of the active strings into fine-bucket order, using the unit-key
-// hash stored with each string.  The bucket-ordered copy is an array of
+// hash and the rank inside its bucket that the producing kernel stored with
+// each string (the value its bucket-count atomic returned), so the position
+// is offsets[bucket] + rank and no atomic is needed here.  The bucket-ordered
+// copy is an array of
 // records of whole 32-byte sectors -- (x, z, c, h) padded to 64 bytes for
 // W = 2, exactly 32 bytes for W = 1 -- so the scattered writes never leave a
-// partly written sector.  Eight strings per thread keep eight cursor
-// atomics in flight.
+// partly written sector.
 // ---------------------------------------------------------------------------
 constexpr int SCATTER_ILP = 8;
 
@@ -244,7 +245,7 @@ constexpr int record_bytes(int W) { return W == 2 ? 64 : 32; }
 
 template <int W>
 __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n, int fshift,
-                                                        long long* cursor, void* dst) {
+                                                        const long long* __restrict__ offsets, void* dst) {
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
     for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x; base < n;
          base += stride) {
@@ -253,14 +254,16 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
-            h[k] = (i < n) ? src.h[i] : 0ull;
+            h[k] = 0;
+            slot[k] = -1;
+            if (i < n) {
+                h[k] = src.h[i];
+                slot[k] = src.rank[i];
+            }
         }
 #pragma unroll
-        for (int k = 0; k < SCATTER_ILP; ++k) {
-            const long long i = base + (long long)k * blockDim.x;
-            slot[k] = (i < n) ? (long long)atomicAdd((unsigned long long*)&cursor[fine_bucket(h[k], fshift)], 1ull)
-                              : -1;
-        }
+        for (int k = 0; k < SCATTER_ILP; ++k)
+            if (slot[k] >= 0) slot[k] += offsets[fine_bucket(h[k], fshift)];
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
@@ -313,6 +316,7 @@ struct LocalSmem {
     unsigned warp_cnt[LB_WARPS];
     unsigned long long warp_base[2][LB_WARPS];
     long long range[2];
+    int bucket_range[3];
     int n_units;
 };
 
@@ -355,7 +359,7 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
+__global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
     const void* bk, const long long* __restrict__ offsets, int n_fine, const __grid_constant__ RxRun run,
     int pass, StrList done, StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift,
     unsigned long long* pop_delta) {
@@ -364,7 +368,8 @@ __global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(run.delta);
 
-    // ---- range: whole buckets whose start lies in [j*T, (j+1)*T)
+    // ---- range: whole buckets whose start lies in [j*T, (j+1)*T), processed
+    // in sub-ranges of whole buckets that fit in shared memory
     if (tid < 2) {
         const long long target = ((long long)blockIdx.x + tid) * LB_TARGET;
         int lo = 0, hi = n_fine;  // first b in [0, n_fine] with offsets[b] >= target
@@ -375,18 +380,40 @@ __global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
             else
                 lo = mid + 1;
         }
-        S.range[tid] = offsets[lo];
+        S.bucket_range[tid] = lo;
     }
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) S.blk_delta[t] = 0;
+    __syncthreads();
+    unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
+    const int b_end = S.bucket_range[1];
+    for (int b_lo = S.bucket_range[0]; b_lo < b_end;) {  // block-uniform
+    __syncthreads();  // everyone has read the previous sub-range's bounds
+    if (tid == 0) {
+        // last bucket boundary b <= b_end with offsets[b] - offsets[b_lo] <= LB_MAX
+        const long long base = offsets[b_lo];
+        int lo = b_lo, hi = b_end;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] - base <= LB_MAX)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        S.range[0] = base;
+        S.range[1] = offsets[lo];
+        S.bucket_range[2] = lo;
+    }
     for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = -1;
     __syncthreads();
     const long long s0 = S.range[0];
     const int m = (int)(S.range[1] - S.range[0]);
-    if (m <= 0) return;
-    if (m > LB_MAX) {
+    const int b_next = S.bucket_range[2];
+    if (b_next == b_lo) {  // one bucket alone exceeds LB_MAX
         if (tid == 0) atomicExch(&ctr->bucket_overflow, 1u);
-        return;
+        break;
     }
+    b_lo = b_next;
+    if (m == 0) continue;
 
     // ---- load the range; key of a string = (z, x with the chunk bits cleared)
     for (int i = tid; i < m; i += LB_THREADS) {
@@ -467,7 +494,6 @@ __global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
     const int n_units = S.n_units;
 
     // ---- rounds: warp wp owns units rbase + wp*LB_UPW + lane for lanes < LB_UPW
-    unsigned long long my_branch = 0, my_drop = 0;
     const int ub = wp * LB_UPW;  // first unit row of this warp
     for (int rbase = 0; rbase < n_units; rbase += LB_RU) {
         const int u = rbase + ub + lane;
@@ -527,6 +553,8 @@ __global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
             unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
             const unsigned n1 = tot & 0xffffu, n2 = tot >> 16;
             unsigned o1 = o12 & 0xffffu, o2 = o12 >> 16;
+            my_one += n1;
+            my_two += n2;
             for (unsigned b = sgl; b; b &= b - 1) {
                 const int l = __ffs(b) - 1;
                 S.list1[wp][o1++] = (uint16_t)((lane << 6) | (((hi >> l) & 1u) << 5) | l);
@@ -647,24 +675,31 @@ __global__ void __launch_bounds__(LB_THREADS) k_bucket_local(
                 // may be this pass's bits just set)
                 for (int j = 0; j < np2l; ++j) clear_bit<W>(x2, p2l[j]);
                 h = hash_key<W>(zz, x2);
-                atomicAdd(&fcount_next[fine_bucket(h, fshift)], 1);
             }
+            const int rk = mr ? atomicAdd(&fcount_next[fine_bucket(h, fshift)], 1) : 0;
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, zz);
                 dst.c[slot] = S.dense[ub + L][l];
-                if (mr) dst.h[slot] = h;
+                if (mr) {
+                    dst.h[slot] = h;
+                    dst.rank[slot] = rk;
+                }
             } else {
                 ctr->overflow = 1u;
             }
         }
         __syncwarp();
     }
+    __syncthreads();  // shared arrays are reused by the next sub-range
+    }
     const unsigned nb = __reduce_add_sync(FULL_MASK, (unsigned)my_branch);
     const unsigned nd = __reduce_add_sync(FULL_MASK, (unsigned)my_drop);
     if (lane == 0 && (nb | nd)) {
         atomicAdd(&ctr->branch_events, (unsigned long long)nb);
         atomicAdd(&ctr->dropped, (unsigned long long)nd);
+        atomicAdd(&ctr->pairs_one, my_one);
+        atomicAdd(&ctr->pairs_two, my_two);
     }
     __syncthreads();
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)

@@ -43,6 +43,7 @@ class orqa_stats_t(ctypes.Structure):
     _fields_ = [("n_strings", ctypes.c_int64), ("last_layer_in", ctypes.c_int64),
                 ("last_layer_peak", ctypes.c_int64), ("string_gate_updates", ctypes.c_int64),
                 ("branch_events", ctypes.c_int64), ("dropped", ctypes.c_int64),
+                ("pair_updates_one", ctypes.c_int64), ("pair_updates_two", ctypes.c_int64),
                 ("chunk_passes", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 

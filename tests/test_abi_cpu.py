@@ -63,7 +63,7 @@ def test_gate_array_marshalling():
     assert (arr[1].kind, arr[1].q0, arr[1].q1) == (orqa.ORQA_RZZ, 1, 2)
     assert ctypes.sizeof(orqa.orqa_gate) == 24
     assert ctypes.sizeof(orqa.orqa_config) == 40
-    assert ctypes.sizeof(orqa.orqa_stats_t) == 56
+    assert ctypes.sizeof(orqa.orqa_stats_t) == 72
 
 
 def test_label_encoding_matches_paper_codes():
