@@ -61,6 +61,7 @@ struct orqa_ctx {
     int32_t* fcount[2] = {nullptr, nullptr};
     long long* foffsets = nullptr;
     long long* tile_sums = nullptr;
+    int32_t* range_start = nullptr;    // first bucket of each unit-kernel range
     uint64_t* hash_active = nullptr;   // unit-key hashes of the active list
     int32_t* rank_active = nullptr;    // ranks inside their fine buckets
     void* records = nullptr;           // bucket-ordered copy of the active list
@@ -150,6 +151,7 @@ Layout layout(int n_qubits, long long cap) {
     t += 2 * align_up(F * 4);              // fine counts (two passes)
     t += align_up((F + 1) * 8);            // fine offsets
     t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
+    t += align_up(((size_t)(cap / LB_TARGET) + 2) * 4);  // unit-kernel range starts
     t += align_up(sizeof(Counters));
     t += align_up(MAX_QUBITS * 8);
     t += align_up(EXPECT_BLOCKS * 8);
@@ -426,7 +428,8 @@ orqa_status fine_scan(orqa_ctx* ctx, int k) {
     const int r = prof_begin(ctx, K_SCAN, (double)ctx->n_fine * 20.0);
     k_scan_tiles<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->fcount[k], ctx->foffsets, ctx->tile_sums);
     k_scan_top<<<1, SCAN_THREADS, 0, ctx->stream>>>(ctx->tile_sums, tiles);
-    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->tile_sums, ctx->n_fine);
+    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->tile_sums, ctx->fcount[k], ctx->n_fine,
+                                                         ctx->range_start, LB_TARGET);
     prof_end(ctx, r);
     LAUNCH_CHECK(ctx);
     return ORQA_OK;
@@ -489,7 +492,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         const long long ranges = (n_active + LB_TARGET - 1) / LB_TARGET;
         const int r_lo = prof_begin(ctx, K_LOCAL, 0);
         k_bucket_local<W><<<(unsigned)ranges, LB_THREADS, ctx->local_smem, ctx->stream>>>(
-            ctx->records, ctx->foffsets, ctx->n_fine, run, pass, ctx->buf[D], act, ctx->cap, ctx->ctr,
+            ctx->records, ctx->foffsets, ctx->range_start, run, pass, ctx->buf[D], act, ctx->cap, ctx->ctr,
             ctx->fcount[fc ^ 1], ctx->fshift, ctx->pop_delta);
         prof_end(ctx, r_lo);
         LAUNCH_CHECK(ctx);
@@ -633,6 +636,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->fcount[1] = (int32_t*)p; p += align_up(F * 4);
     ctx->foffsets = (long long*)p; p += align_up((F + 1) * 8);
     ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
+    ctx->range_start = (int32_t*)p; p += align_up(((size_t)(cfg->capacity / LB_TARGET) + 2) * 4);
     ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));
     ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
     ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);

@@ -29,10 +29,11 @@ namespace orqa {
 
 constexpr int LB_THREADS = 256;
 constexpr int LB_WARPS = LB_THREADS / 32;
-constexpr int LB_MAX = 512;         // most strings one CTA range may hold
+constexpr int LB_MAX = 512;         // most strings one CTA sub-range may hold
 constexpr int LB_TARGET = 320;      // strings per CTA range, on average
 constexpr int LB_TABLE = 1024;      // shared-memory hash slots
 constexpr int LB_UPW = 16;          // units a warp owns per round (lanes 0..15)
+constexpr int LB_UPW_LOG = 4;
 constexpr int LB_RU = LB_WARPS * LB_UPW;  // units per round
 constexpr int LB_LIST = LB_UPW * 16;      // most pairs of one level in a warp
 constexpr int SCAN_THREADS = 1024;
@@ -182,13 +183,34 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums,
     if (t == 0) tile_sums[SCAN_TILE] = total;
 }
 
+// Final scan step.  Also derives the CTA ranges of the unit kernel: range j
+// is the buckets whose start offset lies in [j*T, (j+1)*T), so its first
+// bucket is range_start[j] = min{b : offsets[b] >= j*T}.  Bucket b is that
+// first bucket exactly for the j with offsets[b-1] < j*T <= offsets[b]; the
+// end offsets[n] = total closes the last ranges, and range_start[J] = n for
+// J = ceil(total / T).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, const long long* tile_sums,
-                                                           long long n) {
+                                                           const int32_t* counts, long long n,
+                                                           int32_t* range_start, long long T) {
     const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
     const long long add = tile_sums[blockIdx.x];
+    const long long total = tile_sums[SCAN_TILE];
+    const long long J = (total + T - 1) / T;
+    long long prev = (base == 0) ? -1 : offsets[base] + add - counts[base - 1];
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) offsets[base + k] += add;
-    if (blockIdx.x == 0 && threadIdx.x == 0) offsets[n] = tile_sums[SCAN_TILE];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const long long o = offsets[base + k] + add;
+        offsets[base + k] = o;
+        const long long jlo = (prev < 0) ? 0 : prev / T + 1;
+        const long long jhi = min(o / T, J - 1);
+        for (long long j = jlo; j <= jhi; ++j) range_start[j] = (int32_t)(base + k);
+        prev = o;
+    }
+    if (base + SCAN_ITEMS == n) {  // the end bucket boundary
+        offsets[n] = total;
+        for (long long j = prev / T + 1; j <= J - 1; ++j) range_start[j] = (int32_t)n;
+        range_start[J] = (int32_t)n;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -360,7 +382,8 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 
 template <int W>
 __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
-    const void* bk, const long long* __restrict__ offsets, int n_fine, const __grid_constant__ RxRun run,
+    const void* bk, const long long* __restrict__ offsets, const int32_t* __restrict__ range_start,
+    const __grid_constant__ RxRun run,
     int pass, StrList done, StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift,
     unsigned long long* pop_delta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -368,20 +391,10 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(run.delta);
 
-    // ---- range: whole buckets whose start lies in [j*T, (j+1)*T), processed
-    // in sub-ranges of whole buckets that fit in shared memory
-    if (tid < 2) {
-        const long long target = ((long long)blockIdx.x + tid) * LB_TARGET;
-        int lo = 0, hi = n_fine;  // first b in [0, n_fine] with offsets[b] >= target
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (offsets[mid] >= target)
-                hi = mid;
-            else
-                lo = mid + 1;
-        }
-        S.bucket_range[tid] = lo;
-    }
+    // ---- range: whole buckets whose start lies in [j*T, (j+1)*T) (found by
+    // the scan), processed in sub-ranges of whole buckets that fit in shared
+    // memory
+    if (tid < 2) S.bucket_range[tid] = range_start[blockIdx.x + tid];
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) S.blk_delta[t] = 0;
     __syncthreads();
     unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
@@ -630,7 +643,7 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
             // owner lane: last L < LB_UPW with flat(L) <= k
             int lo = 0, hi2 = LB_UPW - 1;
 #pragma unroll
-            for (int step = 0; step < 4; ++step) {
+            for (int step = 0; step < LB_UPW_LOG; ++step) {
                 const int mid = (lo + hi2 + 1) >> 1;
                 const unsigned fm = __shfl_sync(FULL_MASK, flat, mid);
                 if (fm <= k)
