@@ -70,13 +70,18 @@ typedef struct {
 
 /* orqa_config.flags */
 enum {
-    ORQA_FLAG_PROFILE = 1    /* time every kernel launch with CUDA events on the
+    ORQA_FLAG_PROFILE = 1,   /* time every kernel launch with CUDA events on the
                                 context's stream (see orqa_profile) */
+    ORQA_FLAG_RELATIVE = 2   /* relative truncation (Eq. truncation1): the
+                                `delta` of apply_layer / merge_truncate is eps0
+                                and a string is dropped when c == 0 or
+                                |c| <= eps0 * max|c|, the max taken over the
+                                operator after each gate's updates */
 };
 
 typedef struct {
     int32_t n_qubits;        /* 1..128 */
-    int32_t flags;           /* 0 or ORQA_FLAG_PROFILE */
+    int32_t flags;           /* ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE, or 0 */
     int64_t capacity;        /* most strings any intermediate set may hold */
     void* workspace;         /* device buffer, 256-byte aligned */
     uint64_t workspace_bytes;
@@ -137,6 +142,9 @@ orqa_status orqa_set_operator_device(orqa_ctx* ctx, int64_t n, const uint64_t* x
  *     c == 0 or |c| < delta are dropped (the truncation loop of Algorithm 1
  *     with the absolute threshold); the result is the one of that per-gate
  *     schedule, bit for bit.
+ * With ORQA_FLAG_RELATIVE, delta is eps0 and the truncation after every gate
+ * is the relative one (an X layer is then applied one gate at a time, since
+ * the threshold depends on the whole operator after each gate).
  * n_live_out (may be NULL) receives |O| after the layer.  ECAPACITY if an
  * intermediate set would exceed the capacity (operator unchanged). */
 orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates,

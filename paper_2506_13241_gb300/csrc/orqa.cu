@@ -77,6 +77,7 @@ struct orqa_ctx {
     // ORQA_FLAG_PROFILE: CUDA events around every launch, resolved at the
     // next stream synchronisation.
     bool profile = false;
+    bool relative = false;   // ORQA_FLAG_RELATIVE
     std::vector<PendingLaunch> pending;
     std::vector<cudaEvent_t> event_pool;
     long long prof_launches[K_COUNT] = {};
@@ -404,8 +405,8 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         const int dst = (ctx->cur + 1) % 3;
         if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
         const int r = prof_begin(ctx, K_TRUNCATE, 0);
-        k_truncate<W><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, ctx->buf[dst], ctx->cap,
-                                                                     delta, ctx->ctr);
+        k_truncate<W, false><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, ctx->buf[dst], ctx->cap,
+                                                                            delta, ctx->ctr);
         prof_end(ctx, r);
         LAUNCH_CHECK(ctx);
         Counters h{};
@@ -535,6 +536,78 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     return ORQA_OK;
 }
 
+// Relative truncation of Eq. (truncation1): drop c == 0 and |c| <= eps0 *
+// max|c|.  The threshold is eps0 * max formed on the host in FP64, the same
+// product the CPU oracle forms.
+template <int W>
+orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
+    *dropped = 0;
+    if (ctx->n == 0) return ORQA_OK;
+    unsigned long long* mx = (unsigned long long*)ctx->scalar;
+    CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, 8, ctx->stream));
+    k_absmax<<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur].c, ctx->n, mx);
+    LAUNCH_CHECK(ctx);
+    unsigned long long mb = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&mb, mx, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double mval;
+    memcpy(&mval, &mb, 8);
+    const double thr = eps0 * mval;
+    const int dst = (ctx->cur + 1) % 3;
+    if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+    const int r = prof_begin(ctx, K_TRUNCATE, 0);
+    k_truncate<W, true><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->buf[dst],
+                                                                       ctx->cap, thr, ctx->ctr);
+    prof_end(ctx, r);
+    LAUNCH_CHECK(ctx);
+    Counters h{};
+    orqa_status st = sync_counters(ctx, &h);
+    if (st != ORQA_OK) return st;
+    prof_set_bytes(ctx, r, (double)ctx->n * 8.0 + (double)h.n_done * (16.0 * W + 8.0 * (2 * W + 1)));
+    prof_resolve(ctx);
+    if ((st = check_flags(ctx, h, "relative truncation")) != ORQA_OK) return st;
+    *dropped = ctx->n - (long long)h.n_done;
+    ctx->n = (long long)h.n_done;
+    ctx->cur = dst;
+    return ORQA_OK;
+}
+
+// A layer with relative truncation.  ZZ gates keep every |c|, so the max is
+// unchanged through a ZZ layer and one truncation after it equals one after
+// every gate.  X gates are applied one at a time: the gate with exact zeros
+// dropped, then the truncation with the max of the resulting operator.
+template <int W>
+orqa_status apply_layer_relative(orqa_ctx* ctx, const orqa_gate* g, int ng, double eps0) {
+    orqa_stats_t acc{};
+    long long dropped = 0;
+    orqa_status st;
+    if (g[0].kind == ORQA_RZZ) {
+        if ((st = apply_rzz<W>(ctx, g, ng, 0.0)) != ORQA_OK) return st;
+        acc = ctx->stats;
+        if ((st = truncate_relative<W>(ctx, eps0, &dropped)) != ORQA_OK) return st;
+        acc.dropped += dropped;
+    } else {
+        for (int k = 0; k < ng; ++k) {
+            if (k > 0 && g[k].q0 <= g[k - 1].q0)
+                return fail(ctx, ORQA_EINVAL, "ORQA_RX gates of one layer must have strictly ascending qubits");
+            if ((st = apply_rx<W>(ctx, &g[k], 1, 0.0)) != ORQA_OK) return st;
+            if ((st = truncate_relative<W>(ctx, eps0, &dropped)) != ORQA_OK) return st;
+            const orqa_stats_t& s = ctx->stats;
+            if (k == 0) acc.last_layer_in = s.last_layer_in;
+            acc.last_layer_peak = std::max(acc.last_layer_peak, s.last_layer_peak);
+            acc.string_gate_updates += s.string_gate_updates;
+            acc.branch_events += s.branch_events;
+            acc.dropped += s.dropped + dropped;
+            acc.pair_updates_one += s.pair_updates_one;
+            acc.pair_updates_two += s.pair_updates_two;
+            acc.chunk_passes += s.chunk_passes;
+        }
+    }
+    ctx->stats = acc;
+    ctx->clean_delta = 0.0;
+    return ORQA_OK;
+}
+
 template <int W>
 orqa_status expect_impl(orqa_ctx* ctx, double* out) {
     const int nb = EXPECT_BLOCKS;
@@ -586,7 +659,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     if (!cfg || !out) return ORQA_EINVAL;
     *out = nullptr;
     if (cfg->n_qubits < 1 || cfg->n_qubits > 128 || cfg->capacity < 1 || cfg->capacity > 0x7fffffffLL ||
-        (cfg->flags & ~ORQA_FLAG_PROFILE) != 0 || !cfg->workspace || ((uintptr_t)cfg->workspace % ALIGN) != 0)
+        (cfg->flags & ~(ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE)) != 0 || !cfg->workspace || ((uintptr_t)cfg->workspace % ALIGN) != 0)
         return ORQA_EINVAL;
     const Layout L = layout(cfg->n_qubits, cfg->capacity);
     if (cfg->workspace_bytes < L.total) return ORQA_ENOMEM;
@@ -596,6 +669,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->cap = cfg->capacity;
     ctx->stream = (cudaStream_t)cfg->stream;
     ctx->profile = (cfg->flags & ORQA_FLAG_PROFILE) != 0;
+    ctx->relative = (cfg->flags & ORQA_FLAG_RELATIVE) != 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -685,7 +759,10 @@ orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_ga
         if (kind != ORQA_RX && kind != ORQA_RZZ) return fail(ctx, ORQA_EINVAL, "apply_layer: unknown gate kind");
     }
     orqa_status st;
-    if (kind == ORQA_RZZ)
+    if (ctx->relative)
+        st = (ctx->W == 1) ? apply_layer_relative<1>(ctx, gates, n_gates, delta)
+                           : apply_layer_relative<2>(ctx, gates, n_gates, delta);
+    else if (kind == ORQA_RZZ)
         st = (ctx->W == 1) ? apply_rzz<1>(ctx, gates, n_gates, delta) : apply_rzz<2>(ctx, gates, n_gates, delta);
     else
         st = (ctx->W == 1) ? apply_rx<1>(ctx, gates, n_gates, delta) : apply_rx<2>(ctx, gates, n_gates, delta);
@@ -701,11 +778,19 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
     if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "merge_truncate: bad delta");
     const int dst = (ctx->cur + 1) % 3;
     long long m = 0;
-    orqa_status st = (ctx->W == 1) ? merge_into<1>(ctx, ctx->buf[ctx->cur], ctx->n, dst, delta, &m)
-                                   : merge_into<2>(ctx, ctx->buf[ctx->cur], ctx->n, dst, delta, &m);
+    const double dabs = ctx->relative ? 0.0 : delta;
+    orqa_status st = (ctx->W == 1) ? merge_into<1>(ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m)
+                                   : merge_into<2>(ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m);
     if (st != ORQA_OK) return st;
     ctx->cur = dst;
     ctx->n = m;
+    if (ctx->relative) {
+        long long dropped = 0;
+        st = (ctx->W == 1) ? truncate_relative<1>(ctx, delta, &dropped) : truncate_relative<2>(ctx, delta, &dropped);
+        if (st != ORQA_OK) return st;
+        m = ctx->n;
+        delta = 0.0;
+    }
     if (delta > ctx->clean_delta) ctx->clean_delta = delta;
     ctx->stats.n_strings = m;
     if (n_live_out) *n_live_out = m;

@@ -88,18 +88,22 @@ __global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n, const
 
 // ---------------------------------------------------------------------------
 // Stand-alone truncation (the truncate loop of Algorithm 1): copies the
-// strings with c != 0 and |c| >= delta to dst, order-preserving within a
-// warp, warp-aggregated appends.
+// strings that are kept to dst, order-preserving within a warp,
+// warp-aggregated appends.  Absolute form: keep iff c != 0 and |c| >= delta.
+// Relative form (Eq. truncation1, STRICT): keep iff c != 0 and |c| > thr,
+// thr = eps0 * max|c|.  Both are integer tests on the IEEE bit patterns.
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, bool STRICT>
 __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrList dst,
                                                   long long cap, double delta, Counters* ctr) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         double c = 0.0;
         if (i < n) c = src.c[i];
-        const bool keep = (i < n) && keep_coef(c, delta);
+        const unsigned long long m = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
+        const bool keep = (i < n) && (STRICT ? (m > dbits) : keep_bits(c, dbits));
         const long long slot = warp_append(keep, &ctr->n_done);
         if (keep) {
             if (slot < cap) {
@@ -114,6 +118,18 @@ __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrL
             }
         }
     }
+}
+
+// max |c| as the largest magnitude bit pattern (exact: for non-negative
+// doubles the order of the bit patterns is the order of the values).
+__global__ void __launch_bounds__(256) k_absmax(const double* c, long long n, unsigned long long* out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned long long m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        m = max(m, (unsigned long long)__double_as_longlong(c[i]) & 0x7fffffffffffffffull);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_down_sync(FULL_MASK, m, d));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
 // ---------------------------------------------------------------------------

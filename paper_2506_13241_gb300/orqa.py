@@ -21,6 +21,7 @@ STATUS_NAMES = ["ORQA_OK", "ORQA_EINVAL", "ORQA_ENOMEM", "ORQA_ECAPACITY", "ORQA
                 "ORQA_ETIMEOUT", "ORQA_ESTATE"]
 ORQA_RX, ORQA_RZZ = 1, 2
 ORQA_FLAG_PROFILE = 1
+ORQA_FLAG_RELATIVE = 2
 EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_set_operator_device",
             "orqa_apply_layer", "orqa_merge_truncate", "orqa_expect", "orqa_export", "orqa_stats",
             "orqa_profile_count", "orqa_profile", "orqa_profile_reset",
@@ -250,7 +251,8 @@ class Context:
     uint8 tensor owned by this object; work runs on ``stream`` (a
     torch.cuda.Stream, default: the current stream)."""
 
-    def __init__(self, n_qubits: int, capacity: int, stream=None, device=None, profile: bool = False):
+    def __init__(self, n_qubits: int, capacity: int, stream=None, device=None, profile: bool = False,
+                 relative: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liborqa needs a CUDA device; none is available")
@@ -267,8 +269,8 @@ class Context:
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
             base = self.workspace.data_ptr()
             aligned = (base + 255) // 256 * 256
-            self.ctx = orqa_create(n_qubits, capacity, aligned, nbytes, self.stream.cuda_stream,
-                                   ORQA_FLAG_PROFILE if profile else 0)
+            flags = (ORQA_FLAG_PROFILE if profile else 0) | (ORQA_FLAG_RELATIVE if relative else 0)
+            self.ctx = orqa_create(n_qubits, capacity, aligned, nbytes, self.stream.cuda_stream, flags)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

@@ -74,6 +74,62 @@ def test_table_app_e_exact(orqa, oracle_mod):
     assert np.max(np.abs(np.array(mg) - np.array(table))) < 1e-13
 
 
+@pytest.mark.parametrize("steps", [5])
+def test_relative_truncation_table_column(orqa, oracle_mod, steps):
+    """Relative truncation (Eq. truncation1, ORQA_FLAG_RELATIVE): the App. E
+    Table workload at eps0 = 1e-5, bit-exact against the oracle after every
+    layer, and the printed eps0 = 1e-5 column."""
+    n, edges = W.heavy_hex_eagle()
+    layers = W.kicked_ising_layers(n, edges, 0.9 * math.pi)
+    ctx = orqa.Context(n, 1 << 18, relative=True)
+    ctx.set_labels([(W.z_label(n, [62]), 1.0)])
+    op = oracle_mod.Oracle(n)
+    op.add_label(W.z_label(n, [62]), 1.0)
+    mg = []
+    for t in range(steps):
+        for layer in layers:
+            ctx.apply_layer(layer, 1e-5)
+            for g in layer:
+                op.apply_rel(g, 1e-5)
+            assert_bit_exact(gpu_canonical(ctx, n), oracle_canonical(op, n), "rel step %d" % (t + 1))
+        mg.append(ctx.expect())
+    table = [-0.95105651629515, 0.90450849718747, -0.9423841865631, 0.97438562148434, -0.95311531321393]
+    assert np.max(np.abs(np.array(mg) - np.array(table[:steps]))) < 1e-13
+
+
+def test_relative_truncation_random(orqa, oracle_mod):
+    """Relative truncation on a random 40-qubit operator and layers."""
+    n = 40
+    rng = random.Random(77)
+    labels = _random_labels(rng, n, 80)
+    terms = [(lab, rng.uniform(-1, 1)) for lab in labels]
+    ctx = orqa.Context(n, 1 << 20, relative=True)
+    ctx.set_labels(terms)
+    op = oracle_mod.Oracle(n)
+    for lab, c in terms:
+        op.add_label(lab, c)
+    for step in range(3):
+        edges = set()
+        while len(edges) < 50:
+            a, b = rng.sample(range(n), 2)
+            edges.add((a, b))
+        zz = [("rzz", a, b, -math.pi / 2) for a, b in edges]
+        qs = sorted(rng.sample(range(n), 6))
+        xx = [("rx", q, None, rng.choice([0.3, 0.9, 2.0])) for q in qs]
+        for layer in (zz, xx):
+            ctx.apply_layer(layer, 1e-3)
+            for g in layer:
+                op.apply_rel(g, 1e-3)
+            assert_bit_exact(gpu_canonical(ctx, n), oracle_canonical(op, n), "rel random %d" % step)
+    ctx.merge_truncate(0.05)
+    keys_before = len(op)
+    # relative merge_truncate: drop |c| <= 0.05 max|c| of the merged set
+    mx = op.max_abs()
+    op.truncate(0.0)
+    ref = {k: v for k, v in op.as_dict().items() if abs(v) > 0.05 * mx}
+    assert len(ctx) == len(ref) <= keys_before
+
+
 def test_table_app_e_t5(orqa):
     """t = 5 of the Table (2.1e6 strings): GPU alone against the printed
     eps0 = 0 value and the state vector value."""
