@@ -49,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--capacity", type=float, default=0.0, help="string capacity (0: from workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="fp32: the precision form (FP32 coefficients, compensated pair updates)")
     return ap.parse_args(argv)
 
 
@@ -133,13 +135,13 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def make_gpu_runner(wl, capacity, profile=True):
+def make_gpu_runner(wl, capacity, profile=True, fp32=False):
     import numpy as np
     import torch
     from paper_2506_13241_gb300 import orqa as B
 
     n = wl["n"]
-    ctx = B.Context(n, capacity, profile=profile)
+    ctx = B.Context(n, capacity, profile=profile, fp32=fp32)
     layers = [B.gate_array(layer) for layer in wl["layers"]]
     x_h, z_h = B.strings_from_labels([lab for lab, _ in wl["observable"]], n)
     c_h = np.array([c for _, c in wl["observable"]], dtype=np.float64)
@@ -187,7 +189,7 @@ def run_gpu(args, wl, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     capacity = int(args.capacity) if args.capacity else default_capacity(wl)
-    ctx, step_dev, step_host, h2d, d2h, fp64 = make_gpu_runner(wl, capacity)
+    ctx, step_dev, step_host, h2d, d2h, fp64 = make_gpu_runner(wl, capacity, fp32=(args.precision == "fp32"))
     stream = ctx.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -347,12 +349,30 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
-def workload_config(wl):
+def fp64_magnetization(wl, capacity):
+    """<M_t> of one FP64 evolution on the GPU (the precision form's comparison)."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.empty_cache()
+    _, step_dev, _, _, _, _ = make_gpu_runner(wl, capacity, profile=False, fp32=False)
+    _, mags, _ = step_dev()
+    return mags
+
+
+def error_entry(mags, ref):
+    """|Delta M_t| per step over the steps both runs reached."""
+    k = min(len(mags), len(ref))
+    per_step = [abs(a - b) for a, b in zip(mags[:k], ref[:k])]
+    return {"steps_compared": k, "max_abs": max(per_step) if per_step else None, "per_step": per_step}
+
+
+def workload_config(wl, precision="fp64"):
     return {"workload": wl["name"], "lattice": "heavy-hex 127" if wl["n"] == 127 else "chain %d" % wl["n"],
             "n_qubits": wl["n"], "theta_x": wl["theta_x"], "theta_zz": W.THETA_ZZ,
             "observable": "Z_62" if wl["n"] == 127 else "Z_6", "time_steps": wl["steps"],
             "delta": wl["delta"], "truncation": "absolute |c| < delta after every X gate",
-            "coefficients": "fp64", "l2": "flushed between timed steps"}
+            "coefficients": precision, "l2": "flushed between timed steps"}
 
 
 def main(argv=None):
@@ -388,20 +408,23 @@ def main(argv=None):
         p["launches"] for p in res["prof"] if p["name"] == "expect")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(wl),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic", "config": workload_config(wl, args.precision),
             "roofline": roofline_entry(res["prof"], args.steps),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
             "gpu_launches": launches, "clocks": res["clocks"],
             "magnetization": res["mags"], "peak_strings": res["peak"], "capacity": res["capacity"]}
     line["fp64"] = fp64_entry(res["prof"], res["fp64_ops"], res["clocks"].get("sm_mhz"))
+    if args.precision == "fp32":
+        # The precision form's error per step against the GPU FP64 path on
+        # the same workload (one untimed evolution after the timed run).
+        line["magnetization_error_vs_gpu_fp64"] = error_entry(res["mags"], fp64_magnetization(wl, res["capacity"]))
     if not args.no_cpu_baseline:
         cb = cpu_baseline(wl, args.cpu_seconds)
         om = cb.pop("magnetization")
-        k = min(len(om), len(res["mags"]))
-        line["magnetization_error_vs_oracle"] = {
-            "steps_compared": k, "max_abs": max(abs(a - b) for a, b in zip(res["mags"][:k], om[:k]))}
+        line["magnetization_error_vs_oracle"] = error_entry(res["mags"], om)
         line["cpu_baseline"] = cb
     print(json.dumps(line))
     if world > 1:

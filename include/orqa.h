@@ -72,16 +72,22 @@ typedef struct {
 enum {
     ORQA_FLAG_PROFILE = 1,   /* time every kernel launch with CUDA events on the
                                 context's stream (see orqa_profile) */
-    ORQA_FLAG_RELATIVE = 2   /* relative truncation (Eq. truncation1): the
+    ORQA_FLAG_RELATIVE = 2,  /* relative truncation (Eq. truncation1): the
                                 `delta` of apply_layer / merge_truncate is eps0
                                 and a string is dropped when c == 0 or
                                 |c| <= eps0 * max|c|, the max taken over the
                                 operator after each gate's updates */
+    ORQA_FLAG_FP32 = 4       /* precision form: coefficients stored and
+                                multiplied in FP32; two-member pair updates
+                                (the merges of Algorithm 1) evaluated with the
+                                compensated Dot2 scheme; duplicate merging of
+                                input and <0|O|0> accumulate in FP64.  The ABI
+                                still takes and returns FP64 arrays. */
 };
 
 typedef struct {
     int32_t n_qubits;        /* 1..128 */
-    int32_t flags;           /* ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE, or 0 */
+    int32_t flags;           /* ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE | ORQA_FLAG_FP32, or 0 */
     int64_t capacity;        /* most strings any intermediate set may hold */
     void* workspace;         /* device buffer, 256-byte aligned */
     uint64_t workspace_bytes;

@@ -78,6 +78,7 @@ struct orqa_ctx {
     // next stream synchronisation.
     bool profile = false;
     bool relative = false;   // ORQA_FLAG_RELATIVE
+    bool fp32 = false;       // ORQA_FLAG_FP32: coefficients stored as float
     std::vector<PendingLaunch> pending;
     std::vector<cudaEvent_t> event_pool;
     long long prof_launches[K_COUNT] = {};
@@ -180,6 +181,11 @@ orqa_status fail(orqa_ctx* ctx, orqa_status st, const std::string& msg) {
             return fail(ctx, ORQA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
     } while (0)
 
+// Calls FN<W, T>(args) for the context's plane width and coefficient type.
+#define ORQA_DISPATCH(ctx, FN, ...)                                                          \
+    ((ctx)->W == 1 ? ((ctx)->fp32 ? FN<1, float>(__VA_ARGS__) : FN<1, double>(__VA_ARGS__)) \
+                   : ((ctx)->fp32 ? FN<2, float>(__VA_ARGS__) : FN<2, double>(__VA_ARGS__)))
+
 // cos and sin of a rotation angle, exact (0, +-1) within 1e-12 of a
 // multiple of pi/2.
 void cos_sin(double theta, double* c, double* s, bool* clifford) {
@@ -196,6 +202,61 @@ void cos_sin(double theta, double* c, double* s, bool* clifford) {
     *c = std::cos(theta);
     *s = std::sin(theta);
     *clifford = false;
+}
+
+// Threshold bits for the integer truncation tests of the stored type T:
+// ge_bits<T>(d): |c| >= d  <=>  mag(c) >= ge_bits;  gt_bits<T>(d): |c| > d
+// <=> mag(c) > gt_bits.  For FP32 the threshold is rounded up (resp. down)
+// to a float, so the test on the float value equals the test against d.
+unsigned long long mag64(double d) {
+    unsigned long long b;
+    memcpy(&b, &d, 8);
+    return b & 0x7fffffffffffffffull;
+}
+
+unsigned long long mag32(float f) {
+    unsigned b;
+    memcpy(&b, &f, 4);
+    return (unsigned long long)(b & 0x7fffffffu);
+}
+
+template <typename T>
+unsigned long long ge_bits(double d);
+template <>
+unsigned long long ge_bits<double>(double d) { return mag64(d); }
+template <>
+unsigned long long ge_bits<float>(double d) {
+    float f = (float)d;
+    if ((double)f < d) f = std::nextafter(f, INFINITY);
+    return mag32(f);
+}
+
+template <typename T>
+unsigned long long gt_bits(double d);
+template <>
+unsigned long long gt_bits<double>(double d) { return mag64(d); }
+template <>
+unsigned long long gt_bits<float>(double d) {
+    float f = (float)d;
+    if ((double)f > d) f = std::nextafter(f, 0.0f);
+    return mag32(f);
+}
+
+// Magnitude bits of type T back to a double.
+template <typename T>
+double from_mag(unsigned long long b);
+template <>
+double from_mag<double>(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, 8);
+    return d;
+}
+template <>
+double from_mag<float>(unsigned long long b) {
+    const unsigned u = (unsigned)b;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
 }
 
 int grid_for(const orqa_ctx* ctx, long long n, int block = 256, int per_sm = 8) {
@@ -274,7 +335,13 @@ orqa_status check_flags(orqa_ctx* ctx, const Counters& h, const char* what) {
     return ORQA_OK;
 }
 
-template <int W>
+// Bytes of one string in the SoA buffers: x and z planes plus the coefficient.
+template <int W, typename T>
+constexpr double string_bytes() {
+    return 16.0 * W + (double)sizeof(T);
+}
+
+template <int W, typename Tin, typename Tout>
 orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, double delta,
                        long long* n_out) {
     const long long tcap = std::min(pow2_at_least(2 * (n > 0 ? n : 1)), ctx->table_cap);
@@ -294,12 +361,14 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
         prof_end(ctx, r_off);
         LAUNCH_CHECK(ctx);
         r_sc = prof_begin(ctx, K_MERGE_SCATTER, (double)n * 32.0);
-        k_merge_scatter<<<g, 256, 0, ctx->stream>>>(src.c, n, ctx->uid, ctx->rank, ctx->unit_off, ctx->sorted_c);
+        k_merge_scatter<Tin><<<g, 256, 0, ctx->stream>>>(reinterpret_cast<const Tin*>(src.c), n, ctx->uid, ctx->rank,
+                                                          ctx->unit_off, ctx->sorted_c);
         prof_end(ctx, r_sc);
         LAUNCH_CHECK(ctx);
         r_red = prof_begin(ctx, K_MERGE_REDUCE, 0);
-        k_merge_reduce<W><<<g, 256, 0, ctx->stream>>>(ctx->unit_z, ctx->unit_xb, ctx->unit_count, ctx->unit_off,
-                                                       ctx->sorted_c, delta, ctx->buf[dst_buf], ctx->cap, ctx->ctr);
+        k_merge_reduce<W, Tout><<<g, 256, 0, ctx->stream>>>(ctx->unit_z, ctx->unit_xb, ctx->unit_count,
+                                                             ctx->unit_off, ctx->sorted_c, ge_bits<Tout>(delta),
+                                                             ctx->buf[dst_buf], ctx->cap, ctx->ctr);
         prof_end(ctx, r_red);
         LAUNCH_CHECK(ctx);
     }
@@ -307,7 +376,7 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
     orqa_status st = sync_counters(ctx, &h);
     if (st != ORQA_OK) return st;
     {
-        const double R = 8.0 * (2 * W + 1), nu = (double)h.n_units, nn = (double)n;
+        const double R = string_bytes<W, Tout>(), nu = (double)h.n_units, nn = (double)n;
         prof_set_bytes(ctx, r_as, nn * (32.0 * W + 12.0) + nu * (16.0 * W + 4.0));
         prof_set_bytes(ctx, r_off, nu * 12.0);
         prof_set_bytes(ctx, r_red, nu * (16.0 * W + 12.0) + nn * 8.0 + (double)h.n_done * R);
@@ -380,7 +449,7 @@ orqa_status build_zz_groups(orqa_ctx* ctx, const orqa_gate* g, int ng, std::vect
     return ORQA_OK;
 }
 
-template <int W>
+template <int W, typename T>
 orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     std::vector<ZZGroups> launches;
     orqa_status bst = build_zz_groups(ctx, g, ng, launches);
@@ -388,8 +457,8 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     StrList s = ctx->buf[ctx->cur];
     for (const ZZGroups& l : launches) {
         if (ctx->n == 0) break;
-        const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (8.0 * (2 * W + 1) + 8.0 * W + 8.0));
-        k_rzz_layer<W><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, l);
+        const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T)));
+        k_rzz_layer<W, T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, l);
         prof_end(ctx, r);
         LAUNCH_CHECK(ctx);
     }
@@ -405,14 +474,14 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         const int dst = (ctx->cur + 1) % 3;
         if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
         const int r = prof_begin(ctx, K_TRUNCATE, 0);
-        k_truncate<W, false><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, ctx->buf[dst], ctx->cap,
-                                                                            delta, ctx->ctr);
+        k_truncate<W, T, false><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, ctx->buf[dst], ctx->cap,
+                                                                               ge_bits<T>(delta), ctx->ctr);
         prof_end(ctx, r);
         LAUNCH_CHECK(ctx);
         Counters h{};
         orqa_status st = sync_counters(ctx, &h);
         if (st != ORQA_OK) return st;
-        prof_set_bytes(ctx, r, (double)ctx->n * 8.0 + (double)h.n_done * (16.0 * W + 8.0 * (2 * W + 1)));
+        prof_set_bytes(ctx, r, (double)ctx->n * sizeof(T) + (double)h.n_done * (16.0 * W + string_bytes<W, T>()));
         prof_resolve(ctx);
         if ((st = check_flags(ctx, h, "truncate")) != ORQA_OK) return st;
         ctx->stats.dropped = ctx->n - (long long)h.n_done;
@@ -436,10 +505,12 @@ orqa_status fine_scan(orqa_ctx* ctx, int k) {
     return ORQA_OK;
 }
 
-template <int W>
+template <int W, typename T>
 orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     RxRun run{};
     run.delta = delta;
+    run.dbits64 = ge_bits<double>(delta);
+    run.dbits32 = (uint32_t)ge_bits<float>(delta);
     run.q_first = g[0].q0;
     for (int k = 0; k < ng; ++k) {
         const int q = g[k].q0;
@@ -448,8 +519,10 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         run.mask[q >> 6] |= 1ull << (q & 63);
         bool cl;
         cos_sin(g[k].theta, &run.cs[q], &run.sn[q], &cl);
+        run.csf[q] = (float)run.cs[q];
+        run.snf[q] = (float)run.sn[q];
     }
-    const double R = 8.0 * (2 * W + 1);
+    const double R = string_bytes<W, T>();
     const int S = ctx->cur;
     const int D = (S + 1) % 3;
     StrList act = ctx->buf[(S + 2) % 3];
@@ -463,7 +536,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     int r_split = -1;
     if (n_in > 0) {
         r_split = prof_begin(ctx, K_SPLIT, 0);
-        k_rx_split<W><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[S], n_in, ctx->buf[D], act,
+        k_rx_split<W, T><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[S], n_in, ctx->buf[D], act,
                                                                    ctx->cap, run, ctx->ctr, ctx->fcount[fc],
                                                                    ctx->fshift);
         prof_end(ctx, r_split);
@@ -472,8 +545,8 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     Counters h{};
     orqa_status st = sync_counters(ctx, &h);
     if (st != ORQA_OK) return st;
-    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + 8.0) + (double)(h.n_done + h.n_next) * (8.0 * W + R) +
-                                     (double)h.n_next * 8.0);
+    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + sizeof(T)) + (double)(h.n_done + h.n_next) * (8.0 * W + R) +
+                                     (double)h.n_next * 12.0);
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
     const unsigned long long split_dropped = h.dropped;
@@ -486,20 +559,20 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         CUDA_TRY(ctx, cudaMemsetAsync(&ctx->ctr->n_next, 0, sizeof(unsigned long long), ctx->stream));
         const unsigned long long done_before = h.n_done;
         const int r_sc = prof_begin(ctx, K_BUCKET_SCATTER, (double)n_active * (R + 12.0 + record_bytes(W)));
-        k_bucket_scatter<W><<<grid_for(ctx, (n_active + SCATTER_ILP - 1) / SCATTER_ILP), 256, 0, ctx->stream>>>(
+        k_bucket_scatter<W, T><<<grid_for(ctx, (n_active + SCATTER_ILP - 1) / SCATTER_ILP), 256, 0, ctx->stream>>>(
             act, n_active, ctx->fshift, ctx->foffsets, ctx->records);
         prof_end(ctx, r_sc);
         LAUNCH_CHECK(ctx);
         const long long ranges = (n_active + LB_TARGET - 1) / LB_TARGET;
         const int r_lo = prof_begin(ctx, K_LOCAL, 0);
-        k_bucket_local<W><<<(unsigned)ranges, LB_THREADS, ctx->local_smem, ctx->stream>>>(
+        k_bucket_local<W, T><<<(unsigned)ranges, LB_THREADS, ctx->local_smem, ctx->stream>>>(
             ctx->records, ctx->foffsets, ctx->range_start, run, pass, ctx->buf[D], act, ctx->cap, ctx->ctr,
             ctx->fcount[fc ^ 1], ctx->fshift, ctx->pop_delta);
         prof_end(ctx, r_lo);
         LAUNCH_CHECK(ctx);
         if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
         const double outs = (double)(h.n_done - done_before) + (double)h.n_next;
-        prof_set_bytes(ctx, r_lo, (double)n_active * record_bytes(W) + outs * R + (double)h.n_next * 8.0);
+        prof_set_bytes(ctx, r_lo, (double)n_active * record_bytes(W) + outs * R + (double)h.n_next * 12.0);
         prof_resolve(ctx);
         if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
         if (h.bucket_overflow)
@@ -539,31 +612,31 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
 // Relative truncation of Eq. (truncation1): drop c == 0 and |c| <= eps0 *
 // max|c|.  The threshold is eps0 * max formed on the host in FP64, the same
 // product the CPU oracle forms.
-template <int W>
+template <int W, typename T>
 orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
     *dropped = 0;
     if (ctx->n == 0) return ORQA_OK;
     unsigned long long* mx = (unsigned long long*)ctx->scalar;
     CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, 8, ctx->stream));
-    k_absmax<<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur].c, ctx->n, mx);
+    k_absmax<T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(reinterpret_cast<const T*>(ctx->buf[ctx->cur].c),
+                                                                ctx->n, mx);
     LAUNCH_CHECK(ctx);
     unsigned long long mb = 0;
     CUDA_TRY(ctx, cudaMemcpyAsync(&mb, mx, 8, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    double mval;
-    memcpy(&mval, &mb, 8);
+    const double mval = from_mag<T>(mb);
     const double thr = eps0 * mval;
     const int dst = (ctx->cur + 1) % 3;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     const int r = prof_begin(ctx, K_TRUNCATE, 0);
-    k_truncate<W, true><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->buf[dst],
-                                                                       ctx->cap, thr, ctx->ctr);
+    k_truncate<W, T, true><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->buf[dst],
+                                                                          ctx->cap, gt_bits<T>(thr), ctx->ctr);
     prof_end(ctx, r);
     LAUNCH_CHECK(ctx);
     Counters h{};
     orqa_status st = sync_counters(ctx, &h);
     if (st != ORQA_OK) return st;
-    prof_set_bytes(ctx, r, (double)ctx->n * 8.0 + (double)h.n_done * (16.0 * W + 8.0 * (2 * W + 1)));
+    prof_set_bytes(ctx, r, (double)ctx->n * sizeof(T) + (double)h.n_done * (16.0 * W + string_bytes<W, T>()));
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "relative truncation")) != ORQA_OK) return st;
     *dropped = ctx->n - (long long)h.n_done;
@@ -576,22 +649,22 @@ orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
 // unchanged through a ZZ layer and one truncation after it equals one after
 // every gate.  X gates are applied one at a time: the gate with exact zeros
 // dropped, then the truncation with the max of the resulting operator.
-template <int W>
+template <int W, typename T>
 orqa_status apply_layer_relative(orqa_ctx* ctx, const orqa_gate* g, int ng, double eps0) {
     orqa_stats_t acc{};
     long long dropped = 0;
     orqa_status st;
     if (g[0].kind == ORQA_RZZ) {
-        if ((st = apply_rzz<W>(ctx, g, ng, 0.0)) != ORQA_OK) return st;
+        if ((st = apply_rzz<W, T>(ctx, g, ng, 0.0)) != ORQA_OK) return st;
         acc = ctx->stats;
-        if ((st = truncate_relative<W>(ctx, eps0, &dropped)) != ORQA_OK) return st;
+        if ((st = truncate_relative<W, T>(ctx, eps0, &dropped)) != ORQA_OK) return st;
         acc.dropped += dropped;
     } else {
         for (int k = 0; k < ng; ++k) {
             if (k > 0 && g[k].q0 <= g[k - 1].q0)
                 return fail(ctx, ORQA_EINVAL, "ORQA_RX gates of one layer must have strictly ascending qubits");
-            if ((st = apply_rx<W>(ctx, &g[k], 1, 0.0)) != ORQA_OK) return st;
-            if ((st = truncate_relative<W>(ctx, eps0, &dropped)) != ORQA_OK) return st;
+            if ((st = apply_rx<W, T>(ctx, &g[k], 1, 0.0)) != ORQA_OK) return st;
+            if ((st = truncate_relative<W, T>(ctx, eps0, &dropped)) != ORQA_OK) return st;
             const orqa_stats_t& s = ctx->stats;
             if (k == 0) acc.last_layer_in = s.last_layer_in;
             acc.last_layer_peak = std::max(acc.last_layer_peak, s.last_layer_peak);
@@ -608,11 +681,11 @@ orqa_status apply_layer_relative(orqa_ctx* ctx, const orqa_gate* g, int ng, doub
     return ORQA_OK;
 }
 
-template <int W>
+template <int W, typename T>
 orqa_status expect_impl(orqa_ctx* ctx, double* out) {
     const int nb = EXPECT_BLOCKS;
-    const int r = prof_begin(ctx, K_EXPECT, (double)ctx->n * (8.0 * W + 8.0));
-    k_expect_partial<W><<<nb, 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->partials);
+    const int r = prof_begin(ctx, K_EXPECT, (double)ctx->n * (8.0 * W + sizeof(T)));
+    k_expect_partial<W, T><<<nb, 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->partials);
     k_expect_final<<<1, 32, 0, ctx->stream>>>(ctx->partials, nb, ctx->scalar);
     prof_end(ctx, r);
     LAUNCH_CHECK(ctx);
@@ -620,6 +693,18 @@ orqa_status expect_impl(orqa_ctx* ctx, double* out) {
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     prof_resolve(ctx);
     return ORQA_OK;
+}
+
+// Merge of caller input (FP64 coefficients) into the stored type T, and of
+// the operator itself.
+template <int W, typename T>
+orqa_status merge_input(orqa_ctx* ctx, StrList src, long long n, int dst, double delta, long long* m) {
+    return merge_into<W, double, T>(ctx, src, n, dst, delta, m);
+}
+
+template <int W, typename T>
+orqa_status merge_state(orqa_ctx* ctx, StrList src, long long n, int dst, double delta, long long* m) {
+    return merge_into<W, T, T>(ctx, src, n, dst, delta, m);
 }
 
 orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z, const double* c,
@@ -636,7 +721,7 @@ orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t
         CUDA_TRY(ctx, cudaMemcpyAsync(s.c, c, (size_t)n * 8, kind, ctx->stream));
     }
     long long m = 0;
-    orqa_status st = (W == 1) ? merge_into<1>(ctx, s, n, dst, 0.0, &m) : merge_into<2>(ctx, s, n, dst, 0.0, &m);
+    orqa_status st = ORQA_DISPATCH(ctx, merge_input, ctx, s, n, dst, 0.0, &m);
     if (st != ORQA_OK) return st;
     ctx->cur = dst;
     ctx->n = m;
@@ -659,7 +744,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     if (!cfg || !out) return ORQA_EINVAL;
     *out = nullptr;
     if (cfg->n_qubits < 1 || cfg->n_qubits > 128 || cfg->capacity < 1 || cfg->capacity > 0x7fffffffLL ||
-        (cfg->flags & ~(ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE)) != 0 || !cfg->workspace || ((uintptr_t)cfg->workspace % ALIGN) != 0)
+        (cfg->flags & ~(ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE | ORQA_FLAG_FP32)) != 0 || !cfg->workspace || ((uintptr_t)cfg->workspace % ALIGN) != 0)
         return ORQA_EINVAL;
     const Layout L = layout(cfg->n_qubits, cfg->capacity);
     if (cfg->workspace_bytes < L.total) return ORQA_ENOMEM;
@@ -670,6 +755,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->stream = (cudaStream_t)cfg->stream;
     ctx->profile = (cfg->flags & ORQA_FLAG_PROFILE) != 0;
     ctx->relative = (cfg->flags & ORQA_FLAG_RELATIVE) != 0;
+    ctx->fp32 = (cfg->flags & ORQA_FLAG_FP32) != 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -715,12 +801,24 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
     ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);
     ctx->scalar = (double*)p; p += align_up(64);
-    ctx->local_smem = (ctx->W == 1) ? sizeof(LocalSmem<1>) : sizeof(LocalSmem<2>);
-    cudaError_t fe = (ctx->W == 1)
-                         ? cudaFuncSetAttribute(k_bucket_local<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)ctx->local_smem)
-                         : cudaFuncSetAttribute(k_bucket_local<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)ctx->local_smem);
+    cudaError_t fe;
+    if (ctx->W == 1 && !ctx->fp32) {
+        ctx->local_smem = sizeof(LocalSmem<1, double>);
+        fe = cudaFuncSetAttribute(k_bucket_local<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ctx->local_smem);
+    } else if (ctx->W == 1) {
+        ctx->local_smem = sizeof(LocalSmem<1, float>);
+        fe = cudaFuncSetAttribute(k_bucket_local<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ctx->local_smem);
+    } else if (!ctx->fp32) {
+        ctx->local_smem = sizeof(LocalSmem<2, double>);
+        fe = cudaFuncSetAttribute(k_bucket_local<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ctx->local_smem);
+    } else {
+        ctx->local_smem = sizeof(LocalSmem<2, float>);
+        fe = cudaFuncSetAttribute(k_bucket_local<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ctx->local_smem);
+    }
     if (fe != cudaSuccess) {
         delete ctx;
         return ORQA_ECUDA;
@@ -760,12 +858,11 @@ orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_ga
     }
     orqa_status st;
     if (ctx->relative)
-        st = (ctx->W == 1) ? apply_layer_relative<1>(ctx, gates, n_gates, delta)
-                           : apply_layer_relative<2>(ctx, gates, n_gates, delta);
+        st = ORQA_DISPATCH(ctx, apply_layer_relative, ctx, gates, n_gates, delta);
     else if (kind == ORQA_RZZ)
-        st = (ctx->W == 1) ? apply_rzz<1>(ctx, gates, n_gates, delta) : apply_rzz<2>(ctx, gates, n_gates, delta);
+        st = ORQA_DISPATCH(ctx, apply_rzz, ctx, gates, n_gates, delta);
     else
-        st = (ctx->W == 1) ? apply_rx<1>(ctx, gates, n_gates, delta) : apply_rx<2>(ctx, gates, n_gates, delta);
+        st = ORQA_DISPATCH(ctx, apply_rx, ctx, gates, n_gates, delta);
     if (st != ORQA_OK) return st;
     ctx->stats.n_strings = ctx->n;
     if (n_live_out) *n_live_out = ctx->n;
@@ -779,14 +876,13 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
     const int dst = (ctx->cur + 1) % 3;
     long long m = 0;
     const double dabs = ctx->relative ? 0.0 : delta;
-    orqa_status st = (ctx->W == 1) ? merge_into<1>(ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m)
-                                   : merge_into<2>(ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m);
+    orqa_status st = ORQA_DISPATCH(ctx, merge_state, ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m);
     if (st != ORQA_OK) return st;
     ctx->cur = dst;
     ctx->n = m;
     if (ctx->relative) {
         long long dropped = 0;
-        st = (ctx->W == 1) ? truncate_relative<1>(ctx, delta, &dropped) : truncate_relative<2>(ctx, delta, &dropped);
+        st = ORQA_DISPATCH(ctx, truncate_relative, ctx, delta, &dropped);
         if (st != ORQA_OK) return st;
         m = ctx->n;
         delta = 0.0;
@@ -800,7 +896,7 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
 
 orqa_status orqa_expect(orqa_ctx* ctx, double* out) {
     if (!ctx || !out) return ORQA_EINVAL;
-    return (ctx->W == 1) ? expect_impl<1>(ctx, out) : expect_impl<2>(ctx, out);
+    return ORQA_DISPATCH(ctx, expect_impl, ctx, out);
 }
 
 orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c, int64_t* n_out) {
@@ -810,12 +906,17 @@ orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, do
     if (ctx->n > 0 && (!x || !z || !c)) return fail(ctx, ORQA_EINVAL, "export: null array");
     const StrList s = ctx->buf[ctx->cur];
     const size_t n = (size_t)ctx->n;
+    std::vector<float> cf(ctx->fp32 ? n : 0);
     if (n > 0) {
         CUDA_TRY(ctx, cudaMemcpyAsync(x, s.x, n * ctx->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_TRY(ctx, cudaMemcpyAsync(z, s.z, n * ctx->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CUDA_TRY(ctx, cudaMemcpyAsync(c, s.c, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (ctx->fp32)
+            CUDA_TRY(ctx, cudaMemcpyAsync(cf.data(), s.c, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        else
+            CUDA_TRY(ctx, cudaMemcpyAsync(c, s.c, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < cf.size(); ++i) c[i] = (double)cf[i];
     return ORQA_OK;
 }
 

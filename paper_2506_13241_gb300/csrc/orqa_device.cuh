@@ -47,10 +47,13 @@ struct Counters {
 struct RxRun {
     uint64_t mask[2];        // qubits of the run
     int32_t q_first;         // first (lowest) qubit of the run
-    int32_t pad;
+    uint32_t dbits32;        // threshold as FP32 magnitude bits: smallest float >= delta
+    uint64_t dbits64;        // threshold as FP64 magnitude bits
     double delta;            // absolute truncation threshold
     double cs[MAX_QUBITS];   // cos(theta_q), exact at Clifford angles
     double sn[MAX_QUBITS];   // sin(theta_q)
+    float csf[MAX_QUBITS];   // the same, rounded to FP32 on the host
+    float snf[MAX_QUBITS];
 };
 
 // ZZ layer parameters.  Edges of one Clifford mode form a set; a set is
@@ -345,6 +348,75 @@ __device__ __forceinline__ bool keep_coef(double v, double delta) {
 
 __device__ __forceinline__ bool nonzero_bits(double v) {
     return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
+}
+
+// Coefficient types: FP64 (the default) and FP32 (ORQA_FLAG_FP32).  Zero and
+// threshold tests are integer tests on the magnitude bits of the stored
+// type; thresholds arrive as magnitude bits of that type.
+template <typename T>
+struct Coef;
+
+template <>
+struct Coef<double> {
+    __device__ static unsigned long long mag(double v) {
+        return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    }
+    __device__ static double negate(double v) {
+        return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+    }
+    __device__ static unsigned long long to_slot(double v) { return (unsigned long long)__double_as_longlong(v); }
+    __device__ static double from_slot(unsigned long long b) { return __longlong_as_double((long long)b); }
+    __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits64; }
+    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static double cos_of(const RxRun& r, int q) { return r.cs[q]; }
+    __device__ static double sin_of(const RxRun& r, int q) { return r.sn[q]; }
+};
+
+template <>
+struct Coef<float> {
+    __device__ static unsigned long long mag(float v) { return (unsigned long long)(__float_as_uint(v) & 0x7fffffffu); }
+    __device__ static float negate(float v) { return __uint_as_float(__float_as_uint(v) ^ 0x80000000u); }
+    __device__ static unsigned long long to_slot(float v) { return (unsigned long long)__float_as_uint(v); }
+    __device__ static float from_slot(unsigned long long b) { return __uint_as_float((unsigned)b); }
+    __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits32; }
+    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static float cos_of(const RxRun& r, int q) { return r.csf[q]; }
+    __device__ static float sin_of(const RxRun& r, int q) { return r.snf[q]; }
+};
+
+template <typename T>
+__device__ __forceinline__ bool keep_t(T v, unsigned long long tbits) {
+    const unsigned long long m = Coef<T>::mag(v);
+    return m != 0ull && m >= tbits;
+}
+
+template <typename T>
+__device__ __forceinline__ bool nonzero_t(T v) {
+    return Coef<T>::mag(v) != 0ull;
+}
+
+// a*b + c*d in FP32 with the compensated scheme Dot2 (Ogita, Rump, Oishi
+// 2005): exact products by FMA (TwoProduct), exact sum by TwoSum, and the
+// three error terms added before the final rounding.
+__device__ __forceinline__ float dot2f(float a, float b, float c, float d) {
+    const float p = __fmul_rn(a, b), ep = __fmaf_rn(a, b, -p);
+    const float q = __fmul_rn(c, d), eq = __fmaf_rn(c, d, -q);
+    const float s = __fadd_rn(p, q);
+    const float t = __fsub_rn(s, p);
+    const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(s, t)), __fsub_rn(q, t));
+    return __fadd_rn(s, __fadd_rn(es, __fadd_rn(ep, eq)));
+}
+
+// Pair update of Eq. (update_rule) with both members present:
+// (c_Z, c_Y) -> (cos c_Z - sin c_Y, cos c_Y + sin c_Z).
+__device__ __forceinline__ void pair_update(double co, double sn, double a, double b, double& na, double& nb) {
+    na = __dsub_rn(__dmul_rn(co, a), __dmul_rn(sn, b));
+    nb = __dadd_rn(__dmul_rn(co, b), __dmul_rn(sn, a));
+}
+
+__device__ __forceinline__ void pair_update(float co, float sn, float a, float b, float& na, float& nb) {
+    na = dot2f(co, a, -sn, b);
+    nb = dot2f(co, b, sn, a);
 }
 
 }  // namespace orqa

@@ -32,7 +32,7 @@ namespace orqa {
 // (a << d) by a 2-bit carry-save counter.  In place: one read of x, z, c and
 // one write of z, c per string.
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, typename T>
 __global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n, const __grid_constant__ ZZGroups G) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n, const
             }
         }
         store_plane<W>(s.z, i, z);
-        if (neg) s.c[i] = -s.c[i];
+        if (neg) {
+            T* c = reinterpret_cast<T*>(s.c) + i;
+            *c = Coef<T>::negate(*c);
+        }
     }
 }
 
@@ -91,19 +94,21 @@ __global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n, const
 // strings that are kept to dst, order-preserving within a warp,
 // warp-aggregated appends.  Absolute form: keep iff c != 0 and |c| >= delta.
 // Relative form (Eq. truncation1, STRICT): keep iff c != 0 and |c| > thr,
-// thr = eps0 * max|c|.  Both are integer tests on the IEEE bit patterns.
+// thr = eps0 * max|c|.  Both are integer tests on the magnitude bits of the
+// stored type (tbits: the threshold in that type, rounded so that the test
+// on the stored value equals the test against the FP64 threshold).
 // ---------------------------------------------------------------------------
-template <int W, bool STRICT>
+template <int W, typename T, bool STRICT>
 __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrList dst,
-                                                  long long cap, double delta, Counters* ctr) {
+                                                  long long cap, unsigned long long tbits, Counters* ctr) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
-    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
+    const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        double c = 0.0;
-        if (i < n) c = src.c[i];
-        const unsigned long long m = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
-        const bool keep = (i < n) && (STRICT ? (m > dbits) : keep_bits(c, dbits));
+        T c = 0;
+        if (i < n) c = sc[i];
+        const unsigned long long m = Coef<T>::mag(c);
+        const bool keep = (i < n) && (STRICT ? (m > tbits) : keep_t<T>(c, tbits));
         const long long slot = warp_append(keep, &ctr->n_done);
         if (keep) {
             if (slot < cap) {
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrL
                 load_plane<W>(src.z, i, z);
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z);
-                dst.c[slot] = c;
+                reinterpret_cast<T*>(dst.c)[slot] = c;
             } else {
                 ctr->overflow = 1u;
             }
@@ -122,11 +127,12 @@ __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrL
 
 // max |c| as the largest magnitude bit pattern (exact: for non-negative
 // doubles the order of the bit patterns is the order of the values).
-__global__ void __launch_bounds__(256) k_absmax(const double* c, long long n, unsigned long long* out) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(const T* c, long long n, unsigned long long* out) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned long long m = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        m = max(m, (unsigned long long)__double_as_longlong(c[i]) & 0x7fffffffffffffffull);
+        m = max(m, Coef<T>::mag(c[i]));
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_down_sync(FULL_MASK, m, d));
     if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
@@ -236,15 +242,17 @@ __global__ void __launch_bounds__(256) k_merge_offsets(const int32_t* unit_count
     }
 }
 
-// Moves each string's coefficient into its entry's range.
-__global__ void __launch_bounds__(256) k_merge_scatter(const double* c, long long n, const int32_t* uid,
+// Moves each string's coefficient into its entry's range (as FP64: the
+// duplicates of an entry are summed in an FP64 accumulator).
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_merge_scatter(const Tin* c, long long n, const int32_t* uid,
                                                        const int32_t* rank, const long long* unit_off,
                                                        double* sorted_c) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int u = uid[i];
         if (u < 0) continue;
-        sorted_c[unit_off[u] + rank[i]] = c[i];
+        sorted_c[unit_off[u] + rank[i]] = (double)c[i];
     }
 }
 
@@ -252,12 +260,12 @@ __global__ void __launch_bounds__(256) k_merge_scatter(const double* c, long lon
 // Duplicate merge, step 4: one thread per entry sums the coefficients of its
 // equal strings and keeps the sum if it is non-zero and not below delta.
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, typename Tout>
 __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
                                                       const uint64_t* unit_xb,
                                                       const int32_t* unit_count,
                                                       const long long* unit_off,
-                                                      const double* sorted_c, double delta,
+                                                      const double* sorted_c, unsigned long long tbits,
                                                       StrList dst, long long cap, Counters* ctr) {
     const long long nu = (long long)*((volatile unsigned long long*)&ctr->n_units);
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -270,7 +278,8 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
             acc = sorted_c[off];
             for (int e = 1; e < m; ++e) acc = __dadd_rn(acc, sorted_c[off + e]);
         }
-        const bool keep = (u < nu) && keep_coef(acc, delta);
+        const Tout v = (Tout)acc;
+        const bool keep = (u < nu) && keep_t<Tout>(v, tbits);
         const long long slot = warp_append(keep, &ctr->n_done);
         if (keep) {
             if (slot < cap) {
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
                 load_plane<W>(unit_xb, u, x);
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z);
-                dst.c[slot] = acc;
+                reinterpret_cast<Tout*>(dst.c)[slot] = v;
             } else {
                 ctr->overflow = 1u;
             }
@@ -295,15 +304,16 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
 // ---------------------------------------------------------------------------
 constexpr int EXPECT_BLOCKS = 1024;
 
-template <int W>
+template <int W, typename T>
 __global__ void __launch_bounds__(256) k_expect_partial(StrList s, long long n, double* partials) {
     __shared__ double red[8];
     const long long stride = (long long)gridDim.x * blockDim.x;
     double acc = 0.0;
+    const T* __restrict__ c = reinterpret_cast<const T*>(s.c);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint64_t x[W];
         load_plane<W>(s.x, i, x);
-        if (all_zero<W>(x)) acc = __dadd_rn(acc, s.c[i]);
+        if (all_zero<W>(x)) acc = __dadd_rn(acc, (double)c[i]);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(FULL_MASK, acc, d));

@@ -49,26 +49,27 @@ __device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int
 // run's first gate unless that gate acts on it first.  Active strings are
 // counted into their pass-0 fine bucket.
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, typename T>
 __global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrList done, StrList active,
                                                   long long cap, const __grid_constant__ RxRun run,
                                                   Counters* ctr, int32_t* fcount, int fshift) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
-    const unsigned long long dbits = (unsigned long long)__double_as_longlong(run.delta);
+    const unsigned long long dbits = Coef<T>::threshold(run);
+    const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         uint64_t x[W], z[W];
-        double c = 0.0;
+        T c = 0;
         const bool live = i < n;
         bool act = false, keep = false;
         if (live) {
             load_plane<W>(src.z, i, z);
-            c = src.c[i];
+            c = sc[i];
             uint64_t acc = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w) acc |= z[w] & run.mask[w];
             act = acc != 0;
-            keep = keep_bits(c, dbits);
+            keep = keep_t<T>(c, dbits);
             if (act && !keep) {
                 uint64_t f[W];
 #pragma unroll
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrL
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z);
-                dst.c[slot] = c;
+                reinterpret_cast<T*>(dst.c)[slot] = c;
             } else {
                 ctr->overflow = 1u;
             }
@@ -225,25 +226,25 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, c
 // ---------------------------------------------------------------------------
 constexpr int SCATTER_ILP = 8;
 
-template <int W>
+template <int W, typename T>
 __device__ __forceinline__ void store_record(void* base, long long i, const uint64_t (&x)[W],
-                                             const uint64_t (&z)[W], double c, uint64_t h) {
+                                             const uint64_t (&z)[W], T c, uint64_t h) {
     if constexpr (W == 2) {
         ulonglong2* r = reinterpret_cast<ulonglong2*>(base) + 4 * i;
         r[0] = make_ulonglong2(x[0], x[1]);
         r[1] = make_ulonglong2(z[0], z[1]);
-        r[2] = make_ulonglong2((unsigned long long)__double_as_longlong(c), h);
+        r[2] = make_ulonglong2(Coef<T>::to_slot(c), h);
         r[3] = make_ulonglong2(0ull, 0ull);  // completes the second sector
     } else {
         ulonglong2* r = reinterpret_cast<ulonglong2*>(base) + 2 * i;
         r[0] = make_ulonglong2(x[0], z[0]);
-        r[1] = make_ulonglong2((unsigned long long)__double_as_longlong(c), h);
+        r[1] = make_ulonglong2(Coef<T>::to_slot(c), h);
     }
 }
 
-template <int W>
+template <int W, typename T>
 __device__ __forceinline__ void load_record(const void* base, long long i, uint64_t (&x)[W], uint64_t (&z)[W],
-                                            double& c, uint64_t& h) {
+                                            T& c, uint64_t& h) {
     if constexpr (W == 2) {
         const ulonglong2* r = reinterpret_cast<const ulonglong2*>(base) + 4 * i;
         const ulonglong2 a = r[0], b = r[1], d = r[2];
@@ -251,21 +252,21 @@ __device__ __forceinline__ void load_record(const void* base, long long i, uint6
         x[1] = a.y;
         z[0] = b.x;
         z[1] = b.y;
-        c = __longlong_as_double((long long)d.x);
+        c = Coef<T>::from_slot(d.x);
         h = d.y;
     } else {
         const ulonglong2* r = reinterpret_cast<const ulonglong2*>(base) + 2 * i;
         const ulonglong2 a = r[0], d = r[1];
         x[0] = a.x;
         z[0] = a.y;
-        c = __longlong_as_double((long long)d.x);
+        c = Coef<T>::from_slot(d.x);
         h = d.y;
     }
 }
 
 constexpr int record_bytes(int W) { return W == 2 ? 64 : 32; }
 
-template <int W>
+template <int W, typename T>
 __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n, int fshift,
                                                         const long long* __restrict__ offsets, void* dst) {
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n
             uint64_t x[W], z[W];
             load_plane<W>(src.x, i, x);
             load_plane<W>(src.z, i, z);
-            store_record<W>(dst, slot[k], x, z, src.c[i], h[k]);
+            store_record<W, T>(dst, slot[k], x, z, reinterpret_cast<const T*>(src.c)[i], h[k]);
         }
     }
 }
@@ -318,12 +319,12 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n
 // at 2 lanes per clock per SM whatever the active mask) and no thread loops
 // over one unit's members.
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, typename T>
 struct LocalSmem {
     uint64_t sx[W][LB_MAX];     // x with the chunk bits cleared
     uint64_t sz[W][LB_MAX];
-    double sc[LB_MAX];
-    double dense[LB_RU][32];
+    T sc[LB_MAX];
+    T dense[LB_RU][32];
     int32_t table[LB_TABLE];
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
@@ -380,16 +381,16 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     return ((uint64_t)hi << 32) | lo;
 }
 
-template <int W>
+template <int W, typename T>
 __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
     const void* bk, const long long* __restrict__ offsets, const int32_t* __restrict__ range_start,
     const __grid_constant__ RxRun run,
     int pass, StrList done, StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift,
     unsigned long long* pop_delta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LocalSmem<W>& S = *reinterpret_cast<LocalSmem<W>*>(smem_raw);
+    LocalSmem<W, T>& S = *reinterpret_cast<LocalSmem<W, T>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    const unsigned long long dbits = (unsigned long long)__double_as_longlong(run.delta);
+    const unsigned long long dbits = Coef<T>::threshold(run);
 
     // ---- range: whole buckets whose start lies in [j*T, (j+1)*T) (found by
     // the scan), processed in sub-ranges of whole buckets that fit in shared
@@ -431,8 +432,8 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
     // ---- load the range; key of a string = (z, x with the chunk bits cleared)
     for (int i = tid; i < m; i += LB_THREADS) {
         uint64_t x[W], z[W], f[W], h;
-        double c;
-        load_record<W>(bk, s0 + i, x, z, c, h);
+        T c;
+        load_record<W, T>(bk, s0 + i, x, z, c, h);
 #pragma unroll
         for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
         int pos[CHUNK_BITS];
@@ -579,12 +580,12 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 const int ur = ub + (e >> 6), la = e & 31, lb = la | bit;
                 const bool y_side = (e & 32) != 0;
                 const int q = S.hq[ur];
-                const double v = S.dense[ur][y_side ? lb : la];
-                const double p1 = __dmul_rn(run.cs[q], v), p2 = __dmul_rn(run.sn[q], v);
+                const T v = S.dense[ur][y_side ? lb : la];
+                const T p1 = Coef<T>::mul(Coef<T>::cos_of(run, q), v), p2 = Coef<T>::mul(Coef<T>::sin_of(run, q), v);
                 // sigma_z present: (cos c, sin c); sigma_y present: (-sin c, cos c)
-                const double na = y_side ? __longlong_as_double(__double_as_longlong(p2) ^ (long long)0x8000000000000000ull) : p1;
-                const double nb = y_side ? p1 : p2;
-                const bool ka = keep_bits(na, dbits), kb = keep_bits(nb, dbits);
+                const T na = y_side ? Coef<T>::negate(p2) : p1;
+                const T nb = y_side ? p1 : p2;
+                const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
                 S.dense[ur][la] = na;
                 S.dense[ur][lb] = nb;
@@ -597,11 +598,9 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 const int e = S.list2[wp][t];
                 const int ur = ub + (e >> 5), la = e & 31, lb = la | bit;
                 const int q = S.hq[ur];
-                const double co = run.cs[q], sn = run.sn[q];
-                const double a = S.dense[ur][la], b = S.dense[ur][lb];
-                const double na = __dsub_rn(__dmul_rn(co, a), __dmul_rn(sn, b));
-                const double nb = __dadd_rn(__dmul_rn(co, b), __dmul_rn(sn, a));
-                const bool ka = keep_bits(na, dbits), kb = keep_bits(nb, dbits);
+                T na, nb;
+                pair_update(Coef<T>::cos_of(run, q), Coef<T>::sin_of(run, q), S.dense[ur][la], S.dense[ur][lb], na, nb);
+                const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
                 S.dense[ur][la] = na;
                 S.dense[ur][lb] = nb;
@@ -693,7 +692,7 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, zz);
-                dst.c[slot] = S.dense[ub + L][l];
+                reinterpret_cast<T*>(dst.c)[slot] = S.dense[ub + L][l];
                 if (mr) {
                     dst.h[slot] = h;
                     dst.rank[slot] = rk;

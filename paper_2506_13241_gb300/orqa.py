@@ -22,6 +22,7 @@ STATUS_NAMES = ["ORQA_OK", "ORQA_EINVAL", "ORQA_ENOMEM", "ORQA_ECAPACITY", "ORQA
 ORQA_RX, ORQA_RZZ = 1, 2
 ORQA_FLAG_PROFILE = 1
 ORQA_FLAG_RELATIVE = 2
+ORQA_FLAG_FP32 = 4
 EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_set_operator_device",
             "orqa_apply_layer", "orqa_merge_truncate", "orqa_expect", "orqa_export", "orqa_stats",
             "orqa_profile_count", "orqa_profile", "orqa_profile_reset",
@@ -252,7 +253,7 @@ class Context:
     torch.cuda.Stream, default: the current stream)."""
 
     def __init__(self, n_qubits: int, capacity: int, stream=None, device=None, profile: bool = False,
-                 relative: bool = False):
+                 relative: bool = False, fp32: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liborqa needs a CUDA device; none is available")
@@ -269,7 +270,8 @@ class Context:
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
             base = self.workspace.data_ptr()
             aligned = (base + 255) // 256 * 256
-            flags = (ORQA_FLAG_PROFILE if profile else 0) | (ORQA_FLAG_RELATIVE if relative else 0)
+            flags = ((ORQA_FLAG_PROFILE if profile else 0) | (ORQA_FLAG_RELATIVE if relative else 0) |
+                     (ORQA_FLAG_FP32 if fp32 else 0))
             self.ctx = orqa_create(n_qubits, capacity, aligned, nbytes, self.stream.cuda_stream, flags)
 
     def close(self):

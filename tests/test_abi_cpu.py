@@ -53,7 +53,7 @@ def test_create_validates_config_before_touching_cuda(lib):
     assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
     cfg = orqa.orqa_config(12, 0, 100, 4096, 10, 0)    # too small
     assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_ENOMEM
-    cfg = orqa.orqa_config(12, 4, 100, 4096, 1 << 30, 0)  # unknown flag bit
+    cfg = orqa.orqa_config(12, 8, 100, 4096, 1 << 30, 0)  # unknown flag bit
     assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
 
 

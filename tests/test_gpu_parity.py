@@ -130,6 +130,29 @@ def test_relative_truncation_random(orqa, oracle_mod):
     assert len(ctx) == len(ref) <= keys_before
 
 
+@pytest.mark.parametrize("delta", [1e-4, 1e-5])
+def test_fp32_precision_form(orqa, oracle_mod, delta):
+    """ORQA_FLAG_FP32 (BASELINE config 4): coefficients in FP32, two-member
+    pair updates by the compensated Dot2 scheme, FP64 expectation sum.  The
+    magnetization must stay within 1e-6 of the FP64 oracle: each coefficient
+    sees a few hundred FP32 roundings (2^-24 relative) through 5 steps, and
+    cos, sin themselves are rounded to FP32 (1.2e-8 at theta = pi/4)."""
+    n, edges = W.heavy_hex_eagle()
+    layers = W.kicked_ising_layers(n, edges, math.pi / 4)
+    ctx = orqa.Context(n, 1 << 23, fp32=True)
+    ctx.set_labels([(W.z_label(n, [62]), 1.0)])
+    mg = []
+    for _ in range(5):
+        for layer in layers:
+            ctx.apply_layer(layer, delta)
+        mg.append(ctx.expect())
+    mo, op = oracle_mod.run_layers(n, [(W.z_label(n, [62]), 1.0)], layers, 5, delta)
+    err = np.max(np.abs(np.array(mg) - np.array(mo)))
+    assert err < 1e-6, err
+    # the string set may differ only where a coefficient sits at the threshold
+    assert abs(len(ctx) - len(op)) <= 1e-4 * len(op)
+
+
 def test_table_app_e_t5(orqa):
     """t = 5 of the Table (2.1e6 strings): GPU alone against the printed
     eps0 = 0 value and the state vector value."""
