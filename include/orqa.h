@@ -85,13 +85,21 @@ enum {
                                 still takes and returns FP64 arrays. */
 };
 
+/* Most problems one batched context may hold. */
+#define ORQA_MAX_PROBLEMS 4096
+
 typedef struct {
     int32_t n_qubits;        /* 1..128 */
     int32_t flags;           /* ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE | ORQA_FLAG_FP32, or 0 */
-    int64_t capacity;        /* most strings any intermediate set may hold */
+    int64_t capacity;        /* most strings any intermediate set may hold (all problems together) */
     void* workspace;         /* device buffer, 256-byte aligned */
     uint64_t workspace_bytes;
     void* stream;            /* cudaStream_t, or NULL for the default stream */
+    int32_t n_problems;      /* 0 or 1: one operator.  2..ORQA_MAX_PROBLEMS: a batched
+                                context holding that many independent operators
+                                (see "Batched contexts" below); not with
+                                ORQA_FLAG_RELATIVE */
+    int32_t reserved;        /* must be 0 */
 } orqa_config;
 
 typedef struct {
@@ -119,8 +127,12 @@ typedef struct {
 
 typedef struct orqa_ctx orqa_ctx;
 
-/* Bytes of device workspace needed for n_qubits and capacity. */
+/* Bytes of device workspace needed for n_qubits and capacity (one
+ * operator), or 0 for invalid sizes. */
 uint64_t orqa_workspace_bytes(int32_t n_qubits, int64_t capacity);
+
+/* The same for a context of n_problems operators (orqa_config.n_problems). */
+uint64_t orqa_workspace_bytes_batch(int32_t n_qubits, int64_t capacity, int32_t n_problems);
 
 /* Creates a context holding the empty operator.  The workspace and the
  * stream stay owned by the caller.  EINVAL on bad sizes, ENOMEM if the
@@ -187,6 +199,44 @@ const char* orqa_last_error(const orqa_ctx* ctx);
 
 /* Releases the host context (the caller's workspace is not freed). */
 void orqa_destroy(orqa_ctx* ctx);
+
+/* Batched contexts.  A context created with n_problems = P > 1 holds P
+ * independent operators O_0 .. O_{P-1} (for example one per observable and
+ * angle of a parameter sweep) in one set of buffers: every string carries
+ * its problem index, strings of different problems never merge, and each
+ * kernel launch processes all problems together whatever their sizes.  The
+ * plain calls apply to every problem (orqa_apply_layer with the gates'
+ * own angles, orqa_merge_truncate, orqa_stats over all strings); the calls
+ * below add per-problem inputs and outputs.  orqa_expect and
+ * orqa_set_operator(_device) return ORQA_ESTATE / ORQA_EINVAL on a batched
+ * context. */
+
+/* Replaces all operators by the n strings of the HOST arrays x, z, c (as in
+ * orqa_set_operator); problem[i] in [0, P) is the operator string i belongs
+ * to.  Duplicates within one problem are summed. */
+orqa_status orqa_set_operator_batch(orqa_ctx* ctx, int64_t n, const uint64_t* x,
+                                    const uint64_t* z, const double* c,
+                                    const int32_t* problem);
+
+/* orqa_apply_layer with per-problem angles: theta is a HOST array of
+ * P rows of n_gates angles (row p holds problem p's angle for each gate, in
+ * gate order) and replaces the gates' theta.  ORQA_RX layers only (ZZ
+ * layers are the same Clifford layer for every problem: use
+ * orqa_apply_layer). */
+orqa_status orqa_apply_layer_batch(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates,
+                                   const double* theta, double delta, int64_t* n_live_out);
+
+/* <0|O_p|0> for every problem: out is a HOST array of P doubles (P = 1 for
+ * a plain context, where it equals orqa_expect). */
+orqa_status orqa_expect_batch(orqa_ctx* ctx, double* out);
+
+/* Live strings per problem: out is a HOST array of P int64. */
+orqa_status orqa_problem_sizes(orqa_ctx* ctx, int64_t* out);
+
+/* orqa_export plus each string's problem index (problem: cap int32, may be
+ * NULL; all 0 for a plain context). */
+orqa_status orqa_export_batch(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c,
+                              int32_t* problem, int64_t* n_out);
 
 /* Largest operator orqa_expect_noalloc accepts (2^27 strings). */
 #define ORQA_NOALLOC_MAX_STRINGS 134217728LL

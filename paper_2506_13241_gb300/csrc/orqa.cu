@@ -36,6 +36,7 @@ struct PendingLaunch {
 struct orqa_ctx {
     int n_qubits = 0;
     int W = 1;
+    int P = 1;              // problems sharing the context (batched if > 1)
     long long cap = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 1;
@@ -50,6 +51,7 @@ struct orqa_ctx {
     int32_t* rank = nullptr;
     uint64_t* unit_z = nullptr;
     uint64_t* unit_xb = nullptr;
+    uint16_t* unit_pid = nullptr;
     int32_t* unit_count = nullptr;
     long long* unit_off = nullptr;
     double* sorted_c = nullptr;
@@ -58,7 +60,9 @@ struct orqa_ctx {
     // X-layer passes (fine buckets)
     int n_fine = 0;
     int fshift = 0;
-    int32_t* fcount[2] = {nullptr, nullptr};
+    int32_t* fcount = nullptr;
+    int range_target = LB_TARGET;  // strings per unit-kernel range
+    int sub_max = LB_MAX;          // most strings of one shared-memory sub-range
     long long* foffsets = nullptr;
     long long* tile_sums = nullptr;
     int32_t* range_start = nullptr;    // first bucket of each unit-kernel range
@@ -70,6 +74,15 @@ struct orqa_ctx {
     unsigned long long* pop_delta = nullptr;
     double* partials = nullptr;
     double* scalar = nullptr;
+    // batched contexts: per-problem rotation tables, expectation partials,
+    // per-problem outputs
+    double2* rot64 = nullptr;      // ROT_SLOTS tables of P * MAX_QUBITS (cos, sin)
+    float2* rot32 = nullptr;
+    double* batch_partials = nullptr;
+    double* batch_out = nullptr;   // P doubles
+    unsigned long long* sizes_out = nullptr;  // P counters
+    std::vector<double2> rot_host;  // staging for one table
+    std::vector<float2> rot_host32;
 
     orqa_stats_t stats{};
     std::string err;
@@ -108,11 +121,18 @@ long long pow2_at_least(long long v) {
 
 struct Layout {
     size_t str_x, str_c;  // per string buffer: x and z planes, c
+    size_t str_pid;       // per string buffer: problem indices (batched contexts)
     size_t shared;        // region shared by the layer scratch and the merge scratch
     size_t total;
     long long table_cap;  // merge hash table slots
     long long n_fine;
 };
+
+// Rotation tables a batched context holds: one per distinct X layer of a
+// captured program (host-driven layers use slot 0).
+constexpr int ROT_SLOTS = 16;
+// Smallest range target the unit kernel may be tuned to (sizes range_start).
+constexpr int MIN_RANGE_TARGET = 128;
 
 // Fine buckets: about 16 strings each at full capacity, a power of two and a
 // multiple of the scan tile, at most SCAN_TILE tiles.
@@ -129,35 +149,42 @@ size_t layer_scratch_bytes(int W, size_t C) {
     return align_up(C * (size_t)record_bytes(W)) + align_up(C * 8) + align_up(C * 4);
 }
 
-size_t merge_scratch_bytes(int W, size_t C, long long table_cap) {
-    return 2 * align_up(C * 4) + 2 * align_up(C * W * 8) + align_up(C * 4) + 2 * align_up(C * 8) +
-           align_up((size_t)table_cap * 4);
+size_t merge_scratch_bytes(int W, size_t C, long long table_cap, int P) {
+    return 2 * align_up(C * 4) + 2 * align_up(C * W * 8) + (P > 1 ? align_up(C * 2) : 0) + align_up(C * 4) +
+           2 * align_up(C * 8) + align_up((size_t)table_cap * 4);
 }
 
 // Offsets are computed in the same order by orqa_workspace_bytes and
 // orqa_create.
-Layout layout(int n_qubits, long long cap) {
+Layout layout(int n_qubits, long long cap, int P) {
     Layout L{};
     const int W = n_qubits <= 64 ? 1 : 2;
     const size_t C = (size_t)cap;
     L.str_x = align_up(C * W * 8);
     L.str_c = align_up(C * 8);
+    L.str_pid = P > 1 ? align_up(C * 2) : 0;
     // merge table at load factor <= 0.75; the shared region covers both uses
     L.table_cap = pow2_at_least((4 * cap + 2) / 3);
-    L.shared = std::max(layer_scratch_bytes(W, C), merge_scratch_bytes(W, C, L.table_cap));
+    L.shared = std::max(layer_scratch_bytes(W, C), merge_scratch_bytes(W, C, L.table_cap, P));
     L.n_fine = fine_buckets(cap);
     const size_t F = (size_t)L.n_fine;
     size_t t = 0;
-    t += 3 * (2 * L.str_x + L.str_c);     // three string buffers
+    t += 3 * (2 * L.str_x + L.str_c + L.str_pid);  // three string buffers
     t += L.shared;                         // layer / merge scratch
-    t += 2 * align_up(F * 4);              // fine counts (two passes)
+    t += align_up(F * 4);                  // fine counts
     t += align_up((F + 1) * 8);            // fine offsets
     t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
-    t += align_up(((size_t)(cap / LB_TARGET) + 2) * 4);  // unit-kernel range starts
+    t += align_up(((size_t)(cap / MIN_RANGE_TARGET) + 2) * 4);  // unit-kernel range starts
     t += align_up(sizeof(Counters));
     t += align_up(MAX_QUBITS * 8);
     t += align_up(EXPECT_BLOCKS * 8);
     t += align_up(64);
+    if (P > 1) {
+        const size_t tab = (size_t)P * MAX_QUBITS;
+        t += align_up(ROT_SLOTS * tab * 16) + align_up(ROT_SLOTS * tab * 8);  // rotation tables
+        t += align_up((size_t)EXPECT_BATCH_BLOCKS * P * 8);                    // expectation partials
+        t += align_up((size_t)P * 8) + align_up((size_t)P * 8);                // outputs, sizes
+    }
     L.total = t;
     return L;
 }
@@ -317,16 +344,30 @@ orqa_status sync_counters(orqa_ctx* ctx, Counters* h) {
     return ORQA_OK;
 }
 
+// Clears the layer counters and the error bits (the committed operator's
+// size and buffer, n_live and cur, are kept).
 orqa_status reset_counters(orqa_ctx* ctx) {
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->ctr, 0, offsetof(Counters, n_live), ctx->stream));
+    return ORQA_OK;
+}
+
+// Makes buffer `cur` with n strings the committed operator, on the host and
+// on the device.
+orqa_status host_commit(orqa_ctx* ctx, int cur, long long n) {
+    ctx->cur = cur;
+    ctx->n = n;
+    k_set_live<<<1, 32, 0, ctx->stream>>>(ctx->ctr, n, cur);
+    LAUNCH_CHECK(ctx);
     return ORQA_OK;
 }
 
 orqa_status check_flags(orqa_ctx* ctx, const Counters& h, const char* what) {
-    if (h.timeout)
+    if (h.err & ERR_TIMEOUT)
         return fail(ctx, ORQA_ETIMEOUT, std::string(what) + ": a bounded hash-table wait ran out");
-    if (h.table_full) return fail(ctx, ORQA_ECAPACITY, std::string(what) + ": hash table full");
-    if (h.overflow) {
+    if (h.err & ERR_TABLE_FULL) return fail(ctx, ORQA_ECAPACITY, std::string(what) + ": hash table full");
+    if (h.err & ERR_BUCKET_OVERFLOW)
+        return fail(ctx, ORQA_ECAPACITY, std::string(what) + ": a bucket range exceeded the shared-memory capacity");
+    if (h.err & ERR_OVERFLOW) {
         char b[256];
         snprintf(b, sizeof b, "%s: result exceeds capacity %lld (needed at least %llu + %llu)", what,
                  ctx->cap, (unsigned long long)h.n_done, (unsigned long long)h.n_next);
@@ -353,7 +394,7 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
         const int g = grid_for(ctx, n);
         r_as = prof_begin(ctx, K_MERGE_ASSIGN, 0);
         k_merge_assign<W><<<g, 256, 0, ctx->stream>>>(src, n, ctx->table, tcap - 1, ctx->unit_z, ctx->unit_xb,
-                                                       ctx->unit_count, ctx->uid, ctx->rank, ctx->ctr);
+                                                       ctx->unit_pid, ctx->unit_count, ctx->uid, ctx->rank, ctx->ctr);
         prof_end(ctx, r_as);
         LAUNCH_CHECK(ctx);
         r_off = prof_begin(ctx, K_MERGE_OFFSETS, 0);
@@ -366,7 +407,7 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
         prof_end(ctx, r_sc);
         LAUNCH_CHECK(ctx);
         r_red = prof_begin(ctx, K_MERGE_REDUCE, 0);
-        k_merge_reduce<W, Tout><<<g, 256, 0, ctx->stream>>>(ctx->unit_z, ctx->unit_xb, ctx->unit_count,
+        k_merge_reduce<W, Tout><<<g, 256, 0, ctx->stream>>>(ctx->unit_z, ctx->unit_xb, ctx->unit_pid, ctx->unit_count,
                                                              ctx->unit_off, ctx->sorted_c, ge_bits<Tout>(delta),
                                                              ctx->buf[dst_buf], ctx->cap, ctx->ctr);
         prof_end(ctx, r_red);
@@ -458,7 +499,7 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     for (const ZZGroups& l : launches) {
         if (ctx->n == 0) break;
         const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T)));
-        k_rzz_layer<W, T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->n, l);
+        k_rzz_layer<W, T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->cap, ctx->ctr, l);
         prof_end(ctx, r);
         LAUNCH_CHECK(ctx);
     }
@@ -485,29 +526,32 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         prof_resolve(ctx);
         if ((st = check_flags(ctx, h, "truncate")) != ORQA_OK) return st;
         ctx->stats.dropped = ctx->n - (long long)h.n_done;
-        ctx->n = (long long)h.n_done;
-        ctx->cur = dst;
+        if ((st = host_commit(ctx, dst, (long long)h.n_done)) != ORQA_OK) return st;
         ctx->clean_delta = delta;
     }
     return ORQA_OK;
 }
 
 // Exclusive scan of fine-bucket counts fcount[k] into foffsets.
-orqa_status fine_scan(orqa_ctx* ctx, int k) {
+orqa_status fine_scan(orqa_ctx* ctx) {
     const int tiles = ctx->n_fine / SCAN_TILE;
     const int r = prof_begin(ctx, K_SCAN, (double)ctx->n_fine * 20.0);
-    k_scan_tiles<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->fcount[k], ctx->foffsets, ctx->tile_sums);
-    k_scan_top<<<1, SCAN_THREADS, 0, ctx->stream>>>(ctx->tile_sums, tiles);
-    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->tile_sums, ctx->fcount[k], ctx->n_fine,
-                                                         ctx->range_start, LB_TARGET);
+    k_scan_tiles<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->fcount, ctx->foffsets, ctx->tile_sums, ctx->ctr);
+    k_scan_top<<<1, SCAN_THREADS, 0, ctx->stream>>>(ctx->tile_sums, tiles, ctx->ctr);
+    k_scan_add<<<tiles, SCAN_THREADS, 0, ctx->stream>>>(ctx->foffsets, ctx->tile_sums, ctx->fcount, ctx->n_fine,
+                                                         ctx->range_start, ctx->range_target, ctx->ctr);
     prof_end(ctx, r);
     LAUNCH_CHECK(ctx);
     return ORQA_OK;
 }
 
-template <int W, typename T>
-orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
-    RxRun run{};
+// Fills the parameters of an X layer (strictly ascending qubits).  For a
+// batched context with per-problem angles (theta: n_problems rows of ng
+// angles), the (cos, sin) table of every problem is written to rotation
+// table `slot`; otherwise every problem uses the gates' own angles.
+orqa_status build_rx_run(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, const double* theta, int slot,
+                         RxRun& run) {
+    run = RxRun{};
     run.delta = delta;
     run.dbits64 = ge_bits<double>(delta);
     run.dbits32 = (uint32_t)ge_bits<float>(delta);
@@ -522,64 +566,124 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         run.csf[q] = (float)run.cs[q];
         run.snf[q] = (float)run.sn[q];
     }
+    if (ctx->P > 1) {
+        const size_t tab = (size_t)ctx->P * MAX_QUBITS;
+        ctx->rot_host.assign(tab, make_double2(0.0, 0.0));
+        ctx->rot_host32.assign(tab, make_float2(0.f, 0.f));
+        for (int p = 0; p < ctx->P; ++p)
+            for (int k = 0; k < ng; ++k) {
+                const int q = g[k].q0;
+                double c = run.cs[q], sn = run.sn[q];
+                if (theta) {
+                    const double th = theta[(size_t)p * ng + k];
+                    if (!std::isfinite(th)) return fail(ctx, ORQA_EINVAL, "apply_layer_batch: angle not finite");
+                    bool cl;
+                    cos_sin(th, &c, &sn, &cl);
+                }
+                ctx->rot_host[(size_t)p * MAX_QUBITS + q] = make_double2(c, sn);
+                ctx->rot_host32[(size_t)p * MAX_QUBITS + q] = make_float2((float)c, (float)sn);
+            }
+        double2* d64 = ctx->rot64 + (size_t)slot * tab;
+        float2* d32 = ctx->rot32 + (size_t)slot * tab;
+        CUDA_TRY(ctx, cudaMemcpyAsync(d64, ctx->rot_host.data(), tab * sizeof(double2), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(d32, ctx->rot_host32.data(), tab * sizeof(float2), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        run.tab.f64 = d64;
+        run.tab.f32 = d32;
+    }
+    return ORQA_OK;
+}
+
+// String lists of an X layer applied to the operator in buffer S: the
+// output goes to buffer (S + 1) % 3 and the active list of the passes lives
+// in buffer (S + 2) % 3 with the hash and rank arrays.
+struct RxLists {
+    StrList src, done, act;
+    int D;
+};
+
+RxLists rx_lists(orqa_ctx* ctx, int S) {
+    RxLists L;
+    L.src = ctx->buf[S];
+    L.D = (S + 1) % 3;
+    L.done = ctx->buf[L.D];
+    L.act = ctx->buf[(S + 2) % 3];
+    L.act.h = ctx->hash_active;
+    L.act.rank = ctx->rank_active;
+    return L;
+}
+
+int local_grid(const orqa_ctx* ctx, long long n_active) {
+    const long long ranges = (n_active + ctx->range_target - 1) / ctx->range_target;
+    const long long cap = (long long)ctx->sm_count * 3;  // resident CTAs of the unit kernel
+    return (int)std::max(1ll, std::min(ranges, cap));
+}
+
+// One chunk pass (scan, scatter, unit kernel, bookkeeping) on the device;
+// the counts are read on the device, so the grids may be upper bounds.
+template <int W, typename T>
+orqa_status enqueue_pass(orqa_ctx* ctx, const RxLists& L, const RxRun& run, int scatter_grid, int local_grid_n,
+                         cudaGraphConditionalHandle cond, int use_cond, int* r_sc, int* r_lo) {
+    orqa_status st = fine_scan(ctx);
+    if (st != ORQA_OK) return st;
+    *r_sc = prof_begin(ctx, K_BUCKET_SCATTER, 0);
+    k_bucket_scatter<W, T><<<scatter_grid, 256, 0, ctx->stream>>>(L.act, ctx->cap, ctx->fshift, ctx->foffsets,
+                                                                   ctx->records, ctx->fcount, ctx->n_fine, ctx->ctr);
+    prof_end(ctx, *r_sc);
+    LAUNCH_CHECK(ctx);
+    *r_lo = prof_begin(ctx, K_LOCAL, 0);
+    k_bucket_local<W, T><<<local_grid_n, LB_THREADS, ctx->local_smem, ctx->stream>>>(
+        ctx->records, ctx->foffsets, ctx->range_start, ctx->n_fine, ctx->range_target, ctx->sub_max, run, L.done,
+        L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
+    prof_end(ctx, *r_lo);
+    LAUNCH_CHECK(ctx);
+    k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 0, cond, use_cond);
+    LAUNCH_CHECK(ctx);
+    return ORQA_OK;
+}
+
+template <int W, typename T>
+orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, const double* theta) {
+    RxRun run;
+    orqa_status st = build_rx_run(ctx, g, ng, delta, theta, 0, run);
+    if (st != ORQA_OK) return st;
     const double R = string_bytes<W, T>();
-    const int S = ctx->cur;
-    const int D = (S + 1) % 3;
-    StrList act = ctx->buf[(S + 2) % 3];
-    act.h = ctx->hash_active;
-    act.rank = ctx->rank_active;
+    const RxLists L = rx_lists(ctx, ctx->cur);
     const long long n_in = ctx->n;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
-    int fc = 0;
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount[fc], 0, (size_t)ctx->n_fine * 4, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 4, ctx->stream));
     int r_split = -1;
     if (n_in > 0) {
         r_split = prof_begin(ctx, K_SPLIT, 0);
-        k_rx_split<W, T><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[S], n_in, ctx->buf[D], act,
-                                                                   ctx->cap, run, ctx->ctr, ctx->fcount[fc],
-                                                                   ctx->fshift);
+        k_rx_split<W, T><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(L.src, L.done, L.act, ctx->cap, run, ctx->ctr,
+                                                                     ctx->fcount, ctx->fshift);
         prof_end(ctx, r_split);
         LAUNCH_CHECK(ctx);
     }
+    k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 1, 0, 0);
+    LAUNCH_CHECK(ctx);
     Counters h{};
-    orqa_status st = sync_counters(ctx, &h);
-    if (st != ORQA_OK) return st;
-    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + sizeof(T)) + (double)(h.n_done + h.n_next) * (8.0 * W + R) +
-                                     (double)h.n_next * 12.0);
+    if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
+    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + sizeof(T)) + (double)(h.n_done + h.n_active) * (8.0 * W + R) +
+                                     (double)h.n_active * 12.0);
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
-    const unsigned long long split_dropped = h.dropped;
-    long long n_active = (long long)h.n_next;
-    long long peak = (long long)h.n_done + n_active;
     int pass = 0;
-    while (n_active > 0) {
-        if ((st = fine_scan(ctx, fc)) != ORQA_OK) return st;
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount[fc ^ 1], 0, (size_t)ctx->n_fine * 4, ctx->stream));
-        CUDA_TRY(ctx, cudaMemsetAsync(&ctx->ctr->n_next, 0, sizeof(unsigned long long), ctx->stream));
+    while (h.n_active > 0) {
+        const long long n_active = (long long)h.n_active;
         const unsigned long long done_before = h.n_done;
-        const int r_sc = prof_begin(ctx, K_BUCKET_SCATTER, (double)n_active * (R + 12.0 + record_bytes(W)));
-        k_bucket_scatter<W, T><<<grid_for(ctx, (n_active + SCATTER_ILP - 1) / SCATTER_ILP), 256, 0, ctx->stream>>>(
-            act, n_active, ctx->fshift, ctx->foffsets, ctx->records);
-        prof_end(ctx, r_sc);
-        LAUNCH_CHECK(ctx);
-        const long long ranges = (n_active + LB_TARGET - 1) / LB_TARGET;
-        const int r_lo = prof_begin(ctx, K_LOCAL, 0);
-        k_bucket_local<W, T><<<(unsigned)ranges, LB_THREADS, ctx->local_smem, ctx->stream>>>(
-            ctx->records, ctx->foffsets, ctx->range_start, run, pass, ctx->buf[D], act, ctx->cap, ctx->ctr,
-            ctx->fcount[fc ^ 1], ctx->fshift, ctx->pop_delta);
-        prof_end(ctx, r_lo);
-        LAUNCH_CHECK(ctx);
+        int r_sc = -1, r_lo = -1;
+        st = enqueue_pass<W, T>(ctx, L, run, grid_for(ctx, (n_active + SCATTER_ILP - 1) / SCATTER_ILP),
+                                local_grid(ctx, n_active), 0, 0, &r_sc, &r_lo);
+        if (st != ORQA_OK) return st;
         if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
-        const double outs = (double)(h.n_done - done_before) + (double)h.n_next;
-        prof_set_bytes(ctx, r_lo, (double)n_active * record_bytes(W) + outs * R + (double)h.n_next * 12.0);
+        const double outs = (double)(h.n_done - done_before) + (double)h.n_active;
+        prof_set_bytes(ctx, r_sc, (double)n_active * (R + 12.0 + record_bytes(W)));
+        prof_set_bytes(ctx, r_lo, (double)n_active * record_bytes(W) + outs * R + (double)h.n_active * 12.0);
         prof_resolve(ctx);
         if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
-        if (h.bucket_overflow)
-            return fail(ctx, ORQA_ECAPACITY, "rotation layer: a bucket range exceeded the shared-memory capacity");
-        n_active = (long long)h.n_next;
-        if ((long long)h.n_done + n_active > peak) peak = (long long)h.n_done + n_active;
-        fc ^= 1;
         ++pass;
     }
     // Sum over the gates of |O| before each gate: |O| changes at gate q by
@@ -593,13 +697,12 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         updates += pop;
         const int q = g[k].q0;
         pop += (long long)pd[q];
-        if (k == 0) pop -= (long long)split_dropped;
+        if (k == 0) pop -= (long long)h.split_dropped;
     }
-    ctx->cur = D;
-    ctx->n = (long long)h.n_done;
+    if ((st = host_commit(ctx, L.D, (long long)h.n_done)) != ORQA_OK) return st;
     ctx->clean_delta = delta;
     ctx->stats.last_layer_in = n_in;
-    ctx->stats.last_layer_peak = peak;
+    ctx->stats.last_layer_peak = (long long)h.peak;
     ctx->stats.string_gate_updates = updates;
     ctx->stats.branch_events = (int64_t)h.branch_events;
     ctx->stats.dropped = (int64_t)h.dropped;
@@ -640,9 +743,7 @@ orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "relative truncation")) != ORQA_OK) return st;
     *dropped = ctx->n - (long long)h.n_done;
-    ctx->n = (long long)h.n_done;
-    ctx->cur = dst;
-    return ORQA_OK;
+    return host_commit(ctx, dst, (long long)h.n_done);
 }
 
 // A layer with relative truncation.  ZZ gates keep every |c|, so the max is
@@ -663,7 +764,7 @@ orqa_status apply_layer_relative(orqa_ctx* ctx, const orqa_gate* g, int ng, doub
         for (int k = 0; k < ng; ++k) {
             if (k > 0 && g[k].q0 <= g[k - 1].q0)
                 return fail(ctx, ORQA_EINVAL, "ORQA_RX gates of one layer must have strictly ascending qubits");
-            if ((st = apply_rx<W, T>(ctx, &g[k], 1, 0.0)) != ORQA_OK) return st;
+            if ((st = apply_rx<W, T>(ctx, &g[k], 1, 0.0, nullptr)) != ORQA_OK) return st;
             if ((st = truncate_relative<W, T>(ctx, eps0, &dropped)) != ORQA_OK) return st;
             const orqa_stats_t& s = ctx->stats;
             if (k == 0) acc.last_layer_in = s.last_layer_in;
@@ -681,15 +782,33 @@ orqa_status apply_layer_relative(orqa_ctx* ctx, const orqa_gate* g, int ng, doub
     return ORQA_OK;
 }
 
+// <0|O|0> of the committed operator in buffer `cur` into device memory: one
+// double (plain context) or one per problem (batched context).
+template <int W, typename T>
+orqa_status enqueue_expect(orqa_ctx* ctx, int cur, long long n_hint, double* dev_out) {
+    const StrList s = ctx->buf[cur];
+    if (ctx->P > 1) {
+        const size_t sm = (size_t)ctx->P * 8;
+        k_expect_batch_partial<W, T><<<EXPECT_BATCH_BLOCKS, 256, sm, ctx->stream>>>(s, ctx->cap, ctx->ctr, ctx->P,
+                                                                                     ctx->batch_partials);
+        k_expect_batch_final<<<(ctx->P + 255) / 256, 256, 0, ctx->stream>>>(ctx->batch_partials, EXPECT_BATCH_BLOCKS,
+                                                                           ctx->P, dev_out, ctx->ctr);
+    } else {
+        const int r = prof_begin(ctx, K_EXPECT, (double)n_hint * (8.0 * W + sizeof(T)));
+        k_expect_partial<W, T><<<EXPECT_BLOCKS, 256, 0, ctx->stream>>>(s, ctx->cap, ctx->ctr, ctx->partials);
+        k_expect_final<<<1, 32, 0, ctx->stream>>>(ctx->partials, EXPECT_BLOCKS, dev_out, ctx->ctr);
+        prof_end(ctx, r);
+    }
+    LAUNCH_CHECK(ctx);
+    return ORQA_OK;
+}
+
 template <int W, typename T>
 orqa_status expect_impl(orqa_ctx* ctx, double* out) {
-    const int nb = EXPECT_BLOCKS;
-    const int r = prof_begin(ctx, K_EXPECT, (double)ctx->n * (8.0 * W + sizeof(T)));
-    k_expect_partial<W, T><<<nb, 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->n, ctx->partials);
-    k_expect_final<<<1, 32, 0, ctx->stream>>>(ctx->partials, nb, ctx->scalar);
-    prof_end(ctx, r);
-    LAUNCH_CHECK(ctx);
-    CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->scalar, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    double* dev = ctx->P > 1 ? ctx->batch_out : ctx->scalar;
+    orqa_status st = enqueue_expect<W, T>(ctx, ctx->cur, ctx->n, dev);
+    if (st != ORQA_OK) return st;
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, dev, (size_t)ctx->P * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     prof_resolve(ctx);
     return ORQA_OK;
@@ -707,11 +826,23 @@ orqa_status merge_state(orqa_ctx* ctx, StrList src, long long n, int dst, double
     return merge_into<W, T, T>(ctx, src, n, dst, delta, m);
 }
 
+// problem: HOST array of n problem indices (batched contexts), else null.
 orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z, const double* c,
-                     cudaMemcpyKind kind) {
+                     const int32_t* problem, cudaMemcpyKind kind) {
     if (!ctx) return ORQA_EINVAL;
     if (n < 0 || (n > 0 && (!x || !z || !c))) return fail(ctx, ORQA_EINVAL, "set_operator: bad arguments");
     if (n > ctx->cap) return fail(ctx, ORQA_ECAPACITY, "set_operator: n exceeds capacity");
+    if (ctx->P > 1 && n > 0 && !problem)
+        return fail(ctx, ORQA_EINVAL, "set_operator: a batched context takes problem indices (orqa_set_operator_batch)");
+    std::vector<uint16_t> pid16;
+    if (problem) {
+        if (ctx->P > 1) pid16.resize((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            if (problem[i] < 0 || problem[i] >= ctx->P)
+                return fail(ctx, ORQA_EINVAL, "set_operator_batch: problem index out of range");
+            if (ctx->P > 1) pid16[(size_t)i] = (uint16_t)problem[i];
+        }
+    }
     const int W = ctx->W;
     const int stage = (ctx->cur + 1) % 3, dst = (ctx->cur + 2) % 3;
     StrList s = ctx->buf[stage];
@@ -719,12 +850,13 @@ orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t
         CUDA_TRY(ctx, cudaMemcpyAsync(s.x, x, (size_t)n * W * 8, kind, ctx->stream));
         CUDA_TRY(ctx, cudaMemcpyAsync(s.z, z, (size_t)n * W * 8, kind, ctx->stream));
         CUDA_TRY(ctx, cudaMemcpyAsync(s.c, c, (size_t)n * 8, kind, ctx->stream));
+        if (!pid16.empty())
+            CUDA_TRY(ctx, cudaMemcpyAsync(s.pid, pid16.data(), (size_t)n * 2, cudaMemcpyHostToDevice, ctx->stream));
     }
     long long m = 0;
-    orqa_status st = ORQA_DISPATCH(ctx, merge_input, ctx, s, n, dst, 0.0, &m);
+    orqa_status st = ORQA_DISPATCH(ctx, merge_input, ctx, s, n, dst, 0.0, &m);  // waits for the stream
     if (st != ORQA_OK) return st;
-    ctx->cur = dst;
-    ctx->n = m;
+    if ((st = host_commit(ctx, dst, m)) != ORQA_OK) return st;
     ctx->clean_delta = 0.0;
     ctx->stats = orqa_stats_t{};
     ctx->err.clear();
@@ -735,20 +867,32 @@ orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t
 
 extern "C" {
 
+uint64_t orqa_workspace_bytes_batch(int32_t n_qubits, int64_t capacity, int32_t n_problems) {
+    if (n_qubits < 1 || n_qubits > 128 || capacity < 1 || capacity > 0x7fffffffLL || n_problems < 0 ||
+        n_problems > ORQA_MAX_PROBLEMS)
+        return 0;
+    return (uint64_t)layout(n_qubits, capacity, std::max(1, (int)n_problems)).total;
+}
+
 uint64_t orqa_workspace_bytes(int32_t n_qubits, int64_t capacity) {
-    if (n_qubits < 1 || n_qubits > 128 || capacity < 1 || capacity > 0x7fffffffLL) return 0;
-    return (uint64_t)layout(n_qubits, capacity).total;
+    return orqa_workspace_bytes_batch(n_qubits, capacity, 1);
 }
 
 orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     if (!cfg || !out) return ORQA_EINVAL;
     *out = nullptr;
     if (cfg->n_qubits < 1 || cfg->n_qubits > 128 || cfg->capacity < 1 || cfg->capacity > 0x7fffffffLL ||
-        (cfg->flags & ~(ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE | ORQA_FLAG_FP32)) != 0 || !cfg->workspace || ((uintptr_t)cfg->workspace % ALIGN) != 0)
+        (cfg->flags & ~(ORQA_FLAG_PROFILE | ORQA_FLAG_RELATIVE | ORQA_FLAG_FP32)) != 0 || !cfg->workspace ||
+        ((uintptr_t)cfg->workspace % ALIGN) != 0 || cfg->n_problems < 0 || cfg->n_problems > ORQA_MAX_PROBLEMS ||
+        cfg->reserved != 0)
         return ORQA_EINVAL;
-    const Layout L = layout(cfg->n_qubits, cfg->capacity);
+    const int P = std::max(1, (int)cfg->n_problems);
+    // relative truncation takes the max over the whole operator: one problem only
+    if (P > 1 && (cfg->flags & ORQA_FLAG_RELATIVE)) return ORQA_EINVAL;
+    const Layout L = layout(cfg->n_qubits, cfg->capacity, P);
     if (cfg->workspace_bytes < L.total) return ORQA_ENOMEM;
     orqa_ctx* ctx = new orqa_ctx();
+    ctx->P = P;
     ctx->n_qubits = cfg->n_qubits;
     ctx->W = cfg->n_qubits <= 64 ? 1 : 2;
     ctx->cap = cfg->capacity;
@@ -770,6 +914,11 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
         ctx->buf[b].c = (double*)p;   p += L.str_c;
         ctx->buf[b].h = nullptr;
         ctx->buf[b].rank = nullptr;
+        ctx->buf[b].pid = nullptr;
+        if (P > 1) {
+            ctx->buf[b].pid = (uint16_t*)p;
+            p += L.str_pid;
+        }
     }
     {
         // layer scratch and merge scratch: two views of one region
@@ -782,6 +931,10 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
         ctx->rank = (int32_t*)q; q += align_up(C * 4);
         ctx->unit_z = (uint64_t*)q; q += align_up(C * ctx->W * 8);
         ctx->unit_xb = (uint64_t*)q; q += align_up(C * ctx->W * 8);
+        if (P > 1) {
+            ctx->unit_pid = (uint16_t*)q;
+            q += align_up(C * 2);
+        }
         ctx->unit_count = (int32_t*)q; q += align_up(C * 4);
         ctx->unit_off = (long long*)q; q += align_up(C * 8);
         ctx->sorted_c = (double*)q; q += align_up(C * 8);
@@ -792,15 +945,26 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     const size_t F = (size_t)L.n_fine;
     ctx->n_fine = (int)L.n_fine;
     ctx->fshift = 64 - __builtin_ctzll((unsigned long long)L.n_fine);
-    ctx->fcount[0] = (int32_t*)p; p += align_up(F * 4);
-    ctx->fcount[1] = (int32_t*)p; p += align_up(F * 4);
+    ctx->fcount = (int32_t*)p; p += align_up(F * 4);
     ctx->foffsets = (long long*)p; p += align_up((F + 1) * 8);
     ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
-    ctx->range_start = (int32_t*)p; p += align_up(((size_t)(cfg->capacity / LB_TARGET) + 2) * 4);
+    ctx->range_start = (int32_t*)p; p += align_up(((size_t)(cfg->capacity / MIN_RANGE_TARGET) + 2) * 4);
     ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));
     ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
     ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);
     ctx->scalar = (double*)p; p += align_up(64);
+    if (P > 1) {
+        const size_t tab = (size_t)P * MAX_QUBITS;
+        ctx->rot64 = (double2*)p; p += align_up(ROT_SLOTS * tab * 16);
+        ctx->rot32 = (float2*)p; p += align_up(ROT_SLOTS * tab * 8);
+        ctx->batch_partials = (double*)p; p += align_up((size_t)EXPECT_BATCH_BLOCKS * P * 8);
+        ctx->batch_out = (double*)p; p += align_up((size_t)P * 8);
+        ctx->sizes_out = (unsigned long long*)p; p += align_up((size_t)P * 8);
+    }
+    if ((size_t)(p - (char*)cfg->workspace) != L.total) {  // the carve-up must match the layout
+        delete ctx;
+        return ORQA_EINVAL;
+    }
     cudaError_t fe;
     if (ctx->W == 1 && !ctx->fp32) {
         ctx->local_smem = sizeof(LocalSmem<1, double>);
@@ -819,7 +983,9 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
         fe = cudaFuncSetAttribute(k_bucket_local<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)ctx->local_smem);
     }
-    if (fe != cudaSuccess) {
+    // the empty operator, committed in buffer 0
+    if (fe != cudaSuccess || cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         delete ctx;
         return ORQA_ECUDA;
     }
@@ -829,16 +995,27 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
 
 orqa_status orqa_set_operator(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z,
                               const double* c) {
-    return set_from(ctx, n, x, z, c, cudaMemcpyHostToDevice);
+    return set_from(ctx, n, x, z, c, nullptr, cudaMemcpyHostToDevice);
 }
 
 orqa_status orqa_set_operator_device(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z,
                                      const double* c) {
-    return set_from(ctx, n, x, z, c, cudaMemcpyDeviceToDevice);
+    return set_from(ctx, n, x, z, c, nullptr, cudaMemcpyDeviceToDevice);
 }
 
-orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates, double delta,
-                             int64_t* n_live_out) {
+orqa_status orqa_set_operator_batch(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t* z,
+                                    const double* c, const int32_t* problem) {
+    if (!ctx) return ORQA_EINVAL;
+    if (n > 0 && !problem) return fail(ctx, ORQA_EINVAL, "set_operator_batch: null problem array");
+    return set_from(ctx, n, x, z, c, problem, cudaMemcpyHostToDevice);
+}
+
+}  // extern "C"
+
+namespace {
+
+orqa_status apply_layer_impl(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates, const double* theta,
+                             double delta, int64_t* n_live_out) {
     if (!ctx) return ORQA_EINVAL;
     if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(ctx, ORQA_EINVAL, "apply_layer: bad gate array");
     if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "apply_layer: delta must be finite and >= 0");
@@ -856,18 +1033,34 @@ orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_ga
             return fail(ctx, ORQA_EINVAL, "apply_layer: bad second qubit");
         if (kind != ORQA_RX && kind != ORQA_RZZ) return fail(ctx, ORQA_EINVAL, "apply_layer: unknown gate kind");
     }
+    if (theta && kind != ORQA_RX)
+        return fail(ctx, ORQA_EINVAL, "apply_layer_batch: per-problem angles are for ORQA_RX layers only");
     orqa_status st;
     if (ctx->relative)
         st = ORQA_DISPATCH(ctx, apply_layer_relative, ctx, gates, n_gates, delta);
     else if (kind == ORQA_RZZ)
         st = ORQA_DISPATCH(ctx, apply_rzz, ctx, gates, n_gates, delta);
     else
-        st = ORQA_DISPATCH(ctx, apply_rx, ctx, gates, n_gates, delta);
+        st = ORQA_DISPATCH(ctx, apply_rx, ctx, gates, n_gates, delta, theta);
     if (st != ORQA_OK) return st;
     ctx->stats.n_strings = ctx->n;
     if (n_live_out) *n_live_out = ctx->n;
     ctx->err.clear();
     return ORQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates, double delta,
+                             int64_t* n_live_out) {
+    return apply_layer_impl(ctx, gates, n_gates, nullptr, delta, n_live_out);
+}
+
+orqa_status orqa_apply_layer_batch(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates, const double* theta,
+                                   double delta, int64_t* n_live_out) {
+    return apply_layer_impl(ctx, gates, n_gates, theta, delta, n_live_out);
 }
 
 orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out) {
@@ -896,10 +1089,32 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
 
 orqa_status orqa_expect(orqa_ctx* ctx, double* out) {
     if (!ctx || !out) return ORQA_EINVAL;
+    if (ctx->P > 1) return fail(ctx, ORQA_ESTATE, "expect: batched context (use orqa_expect_batch)");
     return ORQA_DISPATCH(ctx, expect_impl, ctx, out);
 }
 
-orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c, int64_t* n_out) {
+orqa_status orqa_expect_batch(orqa_ctx* ctx, double* out) {
+    if (!ctx || !out) return ORQA_EINVAL;
+    return ORQA_DISPATCH(ctx, expect_impl, ctx, out);
+}
+
+orqa_status orqa_problem_sizes(orqa_ctx* ctx, int64_t* out) {
+    if (!ctx || !out) return ORQA_EINVAL;
+    if (ctx->P == 1) {
+        out[0] = ctx->n;
+        return ORQA_OK;
+    }
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->sizes_out, 0, (size_t)ctx->P * 8, ctx->stream));
+    k_problem_sizes<<<grid_for(ctx, ctx->n), 256, (size_t)ctx->P * 4, ctx->stream>>>(
+        ctx->buf[ctx->cur].pid, ctx->cap, ctx->ctr, ctx->P, ctx->sizes_out);
+    LAUNCH_CHECK(ctx);
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->sizes_out, (size_t)ctx->P * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return ORQA_OK;
+}
+
+orqa_status orqa_export_batch(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c, int32_t* problem,
+                              int64_t* n_out) {
     if (!ctx || !n_out) return ORQA_EINVAL;
     *n_out = ctx->n;
     if (ctx->n > cap) return fail(ctx, ORQA_ECAPACITY, "export: operator larger than cap");
@@ -907,6 +1122,7 @@ orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, do
     const StrList s = ctx->buf[ctx->cur];
     const size_t n = (size_t)ctx->n;
     std::vector<float> cf(ctx->fp32 ? n : 0);
+    std::vector<uint16_t> pid16(problem && ctx->P > 1 ? n : 0);
     if (n > 0) {
         CUDA_TRY(ctx, cudaMemcpyAsync(x, s.x, n * ctx->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_TRY(ctx, cudaMemcpyAsync(z, s.z, n * ctx->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -914,10 +1130,18 @@ orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, do
             CUDA_TRY(ctx, cudaMemcpyAsync(cf.data(), s.c, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
         else
             CUDA_TRY(ctx, cudaMemcpyAsync(c, s.c, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (!pid16.empty())
+            CUDA_TRY(ctx, cudaMemcpyAsync(pid16.data(), s.pid, n * 2, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     for (size_t i = 0; i < cf.size(); ++i) c[i] = (double)cf[i];
+    if (problem)
+        for (size_t i = 0; i < n; ++i) problem[i] = pid16.empty() ? 0 : (int32_t)pid16[i];
     return ORQA_OK;
+}
+
+orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c, int64_t* n_out) {
+    return orqa_export_batch(ctx, cap, x, z, c, nullptr, n_out);
 }
 
 orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out) {

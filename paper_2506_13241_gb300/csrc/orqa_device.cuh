@@ -24,9 +24,20 @@ struct StrList {
     double* c;
     uint64_t* h;     // per-string unit-key hash for the next chunk pass (active list only)
     int32_t* rank;   // per-string rank inside its fine bucket (active list only)
+    uint16_t* pid;   // problem index per string (batched contexts), else null
 };
 
-// Device counters shared by the kernels of one call.
+// Error bits of Counters::err.
+constexpr unsigned ERR_OVERFLOW = 1u;         // an append would have exceeded capacity
+constexpr unsigned ERR_TIMEOUT = 2u;          // a bounded spin-wait gave up
+constexpr unsigned ERR_TABLE_FULL = 4u;       // the merge hash table had no free slot
+constexpr unsigned ERR_BUCKET_OVERFLOW = 8u;  // a CTA range exceeded its shared-memory capacity
+
+// Device counters.  The fields before `err` describe the layer (or merge)
+// in progress and are cleared when it starts.  `err` is sticky within a
+// captured program: once set, every later layer kernel returns at once, so
+// the operator of the last completed layer stays intact.  `n_live` is the
+// size of the committed operator; only commit kernels and the host write it.
 struct Counters {
     unsigned long long n_done;       // strings appended to the output list
     unsigned long long n_next;       // strings appended to the next active list
@@ -36,11 +47,31 @@ struct Counters {
     unsigned long long dropped;
     unsigned long long pairs_one;    // pair updates with one member present (2 DMUL)
     unsigned long long pairs_two;    // pair updates with both present (4 DMUL + 2 DADD)
-    unsigned int overflow;           // an append would have exceeded capacity
-    unsigned int timeout;            // a bounded spin-wait gave up
-    unsigned int table_full;         // the hash table had no free slot
-    unsigned int bucket_overflow;    // a CTA range exceeded its shared-memory capacity
-    double expect_partial[1];        // unused placeholder (keeps 8-byte alignment)
+    unsigned long long n_active;     // strings in the active list of the current pass
+    unsigned long long split_dropped;  // strings the entry split dropped
+    unsigned long long peak;         // largest output + active count seen in the layer
+    unsigned int range_cursor;       // next CTA range of the unit kernel
+    int pass;                        // chunk pass in progress
+    unsigned int err;                // ERR_* bits
+    unsigned int n_layers;           // layers committed since the last host reset
+    unsigned long long n_live;       // |O| of the committed operator
+    int cur;                         // buffer holding the committed operator
+    int pad;
+};
+
+// True in every thread of the block iff an error bit is set.  The test is
+// block-uniform (one read, broadcast by the barrier), so a kernel can return
+// on it without leaving a warp or a barrier partly populated.  Every thread
+// of the block must call it.
+__device__ __forceinline__ bool block_aborted(const Counters* ctr) {
+    return __syncthreads_or(threadIdx.x == 0 && *(const volatile unsigned*)&ctr->err != 0u) != 0;
+}
+
+// Per-problem rotation table of a batched X layer: entry p * MAX_QUBITS + q
+// holds (cos, sin) of problem p's angle on qubit q.
+struct RotTable {
+    const double2* f64;
+    const float2* f32;
 };
 
 // Per-layer parameters of a run of X rotations (strictly ascending qubits).
@@ -50,6 +81,7 @@ struct RxRun {
     uint32_t dbits32;        // threshold as FP32 magnitude bits: smallest float >= delta
     uint64_t dbits64;        // threshold as FP64 magnitude bits
     double delta;            // absolute truncation threshold
+    RotTable tab;            // batched contexts: per-problem angles (else null)
     double cs[MAX_QUBITS];   // cos(theta_q), exact at Clifford angles
     double sn[MAX_QUBITS];   // sin(theta_q)
     float csf[MAX_QUBITS];   // the same, rounded to FP32 on the host
@@ -213,15 +245,30 @@ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
 // Hash of a (z, x) key: one odd-constant multiply per word, then the mix64
 // finaliser, whose top bits pick fine buckets and low bits pick shared-memory
 // slots.  Equality is always decided on the full key.
+// `salt` is the problem index in batched contexts (0 otherwise), so equal
+// strings of different problems land in different buckets and slots.
 template <int W>
-__device__ __forceinline__ uint64_t hash_key(const uint64_t (&z)[W], const uint64_t (&xb)[W]) {
+__device__ __forceinline__ uint64_t hash_key(const uint64_t (&z)[W], const uint64_t (&xb)[W],
+                                             unsigned salt = 0) {
     uint64_t h = z[0] * 0x9e3779b97f4a7c15ull ^ (xb[0] * 0xc2b2ae3d27d4eb4full + 0x165667b19e3779f9ull);
     if constexpr (W == 2) {
         h ^= (z[1] * 0xd6e8feb86659fd93ull) ^ ((xb[1] * 0x94d049bb133111ebull) >> 1);
         h += 0x27d4eb2f165667c5ull;
     }
+    h ^= (uint64_t)salt * 0x9fb21c651e98df25ull;
     return mix64(h);
 }
+
+// A unit-key hash carries the string's problem index in bits 16..31; fine
+// buckets use the top bits and shared-memory slots the low 10 bits, so the
+// embedded index changes neither.
+constexpr int PID_SHIFT = 16;
+
+__device__ __forceinline__ uint64_t with_pid(uint64_t h, unsigned pid) {
+    return (h & ~(0xffffull << PID_SHIFT)) | ((uint64_t)(pid & 0xffffu) << PID_SHIFT);
+}
+
+__device__ __forceinline__ unsigned pid_of(uint64_t h) { return (unsigned)(h >> PID_SHIFT) & 0xffffu; }
 
 // Position of the k-th set bit (0-based, k < popcount(v)) of v.
 __device__ __forceinline__ int nth_set_bit(uint64_t v, int k) {
@@ -302,7 +349,7 @@ __device__ __forceinline__ int chunk_positions(const uint64_t (&f)[W], int skip,
 template <int W>
 __device__ __forceinline__ uint64_t unit_key_hash(const uint64_t (&x)[W], const uint64_t (&z)[W],
                                                   const uint64_t* mask, int pass, int (&pos)[CHUNK_BITS],
-                                                  int& np, int& idx, bool& more) {
+                                                  int& np, int& idx, bool& more, unsigned pid = 0) {
     uint64_t f[W], xb[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -315,7 +362,7 @@ __device__ __forceinline__ uint64_t unit_key_hash(const uint64_t (&x)[W], const 
         idx |= bit_of<W>(x, pos[j]) << j;
         clear_bit<W>(xb, pos[j]);
     }
-    return hash_key<W>(z, xb);
+    return with_pid(hash_key<W>(z, xb, pid), pid);
 }
 
 // Warp-aggregated append: every lane of a full warp calls it; lanes with
@@ -368,8 +415,17 @@ struct Coef<double> {
     __device__ static double from_slot(unsigned long long b) { return __longlong_as_double((long long)b); }
     __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits64; }
     __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
-    __device__ static double cos_of(const RxRun& r, int q) { return r.cs[q]; }
-    __device__ static double sin_of(const RxRun& r, int q) { return r.sn[q]; }
+    // (cos, sin) of problem p's angle on qubit q
+    __device__ static void rot(const RxRun& r, unsigned p, int q, double& c, double& s) {
+        if (r.tab.f64) {
+            const double2 v = r.tab.f64[p * MAX_QUBITS + q];
+            c = v.x;
+            s = v.y;
+        } else {
+            c = r.cs[q];
+            s = r.sn[q];
+        }
+    }
 };
 
 template <>
@@ -380,8 +436,16 @@ struct Coef<float> {
     __device__ static float from_slot(unsigned long long b) { return __uint_as_float((unsigned)b); }
     __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits32; }
     __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
-    __device__ static float cos_of(const RxRun& r, int q) { return r.csf[q]; }
-    __device__ static float sin_of(const RxRun& r, int q) { return r.snf[q]; }
+    __device__ static void rot(const RxRun& r, unsigned p, int q, float& c, float& s) {
+        if (r.tab.f32) {
+            const float2 v = r.tab.f32[p * MAX_QUBITS + q];
+            c = v.x;
+            s = v.y;
+        } else {
+            c = r.csf[q];
+            s = r.snf[q];
+        }
+    }
 };
 
 template <typename T>

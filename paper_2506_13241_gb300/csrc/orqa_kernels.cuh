@@ -32,8 +32,12 @@ namespace orqa {
 // (a << d) by a 2-bit carry-save counter.  In place: one read of x, z, c and
 // one write of z, c per string.
 // ---------------------------------------------------------------------------
+// The operator is the committed one (n = n_live strings, read on the device).
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long n, const __grid_constant__ ZZGroups G) {
+__global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long cap, Counters* ctr,
+                                                   const __grid_constant__ ZZGroups G) {
+    if (block_aborted(ctr)) return;
+    const long long n = min((long long)ctr->n_live, cap);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint64_t x[W], z[W];
@@ -118,8 +122,9 @@ __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrL
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z);
                 reinterpret_cast<T*>(dst.c)[slot] = c;
+                if (dst.pid) dst.pid[slot] = src.pid[i];
             } else {
-                ctr->overflow = 1u;
+                atomicOr(&ctr->err, ERR_OVERFLOW);
             }
         }
     }
@@ -149,18 +154,20 @@ __global__ void __launch_bounds__(256) k_absmax(const T* c, long long n, unsigne
 template <int W>
 __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, int32_t* table,
                                                       long long table_mask, uint64_t* unit_z, uint64_t* unit_x,
-                                                      int32_t* unit_count, int32_t* uid_out, int32_t* rank_out,
-                                                      Counters* ctr) {
+                                                      uint16_t* unit_pid, int32_t* unit_count, int32_t* uid_out,
+                                                      int32_t* rank_out, Counters* ctr) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         uint64_t x[W], z[W];
         bool done = i >= n;
         long long slot = 0;
+        unsigned pid = 0;
         if (!done) {
             load_plane<W>(src.x, i, x);
             load_plane<W>(src.z, i, z);
-            slot = (long long)(hash_key<W>(z, x) & (uint64_t)table_mask);
+            if (src.pid) pid = src.pid[i];
+            slot = (long long)(hash_key<W>(z, x, pid) & (uint64_t)table_mask);
         }
         int my_uid = -1;
         long long probes = 0;
@@ -175,6 +182,7 @@ __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, 
             if (claimed) {
                 store_plane<W>(unit_z, u, z);
                 store_plane<W>(unit_x, u, x);
+                if (unit_pid) unit_pid[u] = (uint16_t)pid;
                 unit_count[u] = 0;
                 __threadfence();
                 atomicExch(&table[slot], (int32_t)u);
@@ -189,14 +197,14 @@ __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, 
                     ++spins;
                 }
                 if (v == SLOT_BUSY) {
-                    atomicExch(&ctr->timeout, 1u);
+                    atomicOr(&ctr->err, ERR_TIMEOUT);
                     done = true;
                 } else {
                     __threadfence();
                     uint64_t kz[W], kx[W];
                     load_plane_cg<W>(unit_z, v, kz);
                     load_plane_cg<W>(unit_x, v, kx);
-                    bool eq = true;
+                    bool eq = !unit_pid || __ldcg(unit_pid + v) == (uint16_t)pid;
 #pragma unroll
                     for (int w = 0; w < W; ++w) eq = eq && (kz[w] == z[w]) && (kx[w] == x[w]);
                     if (eq) {
@@ -205,7 +213,7 @@ __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, 
                     } else {
                         slot = (slot + 1) & table_mask;
                         if (++probes > table_mask) {
-                            atomicExch(&ctr->table_full, 1u);
+                            atomicOr(&ctr->err, ERR_TABLE_FULL);
                             done = true;
                         }
                     }
@@ -263,6 +271,7 @@ __global__ void __launch_bounds__(256) k_merge_scatter(const Tin* c, long long n
 template <int W, typename Tout>
 __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
                                                       const uint64_t* unit_xb,
+                                                      const uint16_t* unit_pid,
                                                       const int32_t* unit_count,
                                                       const long long* unit_off,
                                                       const double* sorted_c, unsigned long long tbits,
@@ -289,8 +298,9 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z);
                 reinterpret_cast<Tout*>(dst.c)[slot] = v;
+                if (dst.pid) dst.pid[slot] = unit_pid[u];
             } else {
-                ctr->overflow = 1u;
+                atomicOr(&ctr->err, ERR_OVERFLOW);
             }
         } else if (u < nu) {
             atomicAdd(&ctr->dropped, 1ull);
@@ -304,9 +314,12 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
 // ---------------------------------------------------------------------------
 constexpr int EXPECT_BLOCKS = 1024;
 
+// n = n_live strings of the committed operator, read on the device.
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_expect_partial(StrList s, long long n, double* partials) {
+__global__ void __launch_bounds__(256) k_expect_partial(StrList s, long long cap, const Counters* ctr,
+                                                        double* partials) {
     __shared__ double red[8];
+    const long long n = min((long long)ctr->n_live, cap);
     const long long stride = (long long)gridDim.x * blockDim.x;
     double acc = 0.0;
     const T* __restrict__ c = reinterpret_cast<const T*>(s.c);
@@ -328,14 +341,80 @@ __global__ void __launch_bounds__(256) k_expect_partial(StrList s, long long n, 
 
 // One warp adds the block partials in a fixed order: lane l sums partials
 // l, l+32, ... in sequence, then a fixed shuffle tree combines the lanes.
-__global__ void k_expect_final(const double* partials, int nblocks, double* out) {
+__global__ void k_expect_final(const double* partials, int nblocks, double* out, const Counters* ctr) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32 || blockIdx.x != 0) return;
     double acc = 0.0;
     for (int k = lane; k < nblocks; k += 32) acc = __dadd_rn(acc, partials[k]);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(FULL_MASK, acc, d));
-    if (lane == 0) *out = acc;
+    if (lane == 0) *out = ctr->err ? __longlong_as_double(0x7ff8000000000000ll) : acc;  // NaN after an error
+}
+
+// ---------------------------------------------------------------------------
+// <0|O_p|0> of every problem p of a batched context.  Each block adds the
+// diagonal strings it meets into per-problem shared-memory accumulators;
+// the block partials of problem p are then added in block order.
+// ---------------------------------------------------------------------------
+constexpr int EXPECT_BATCH_BLOCKS = 256;
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_expect_batch_partial(StrList s, long long cap, const Counters* ctr,
+                                                              int n_problems, double* partials) {
+    extern __shared__ double acc_p[];
+    for (int p = threadIdx.x; p < n_problems; p += blockDim.x) acc_p[p] = 0.0;
+    __syncthreads();
+    const long long n = min((long long)ctr->n_live, cap);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const T* __restrict__ c = reinterpret_cast<const T*>(s.c);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint64_t x[W];
+        load_plane<W>(s.x, i, x);
+        if (all_zero<W>(x)) atomicAdd(&acc_p[s.pid[i]], (double)c[i]);
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n_problems; p += blockDim.x)
+        partials[(long long)blockIdx.x * n_problems + p] = acc_p[p];
+}
+
+__global__ void __launch_bounds__(256) k_expect_batch_final(const double* partials, int nblocks, int n_problems,
+                                                            double* out, const Counters* ctr) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_problems) return;
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) acc = __dadd_rn(acc, partials[(long long)b * n_problems + p]);
+    out[p] = ctr->err ? __longlong_as_double(0x7ff8000000000000ll) : acc;  // NaN after an error
+}
+
+// Live strings per problem.
+__global__ void __launch_bounds__(256) k_problem_sizes(const uint16_t* pid, long long cap, const Counters* ctr,
+                                                       int n_problems, unsigned long long* out) {
+    extern __shared__ unsigned cnt_p[];
+    for (int p = threadIdx.x; p < n_problems; p += blockDim.x) cnt_p[p] = 0u;
+    __syncthreads();
+    const long long n = min((long long)ctr->n_live, cap);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt_p[pid[i]], 1u);
+    __syncthreads();
+    for (int p = threadIdx.x; p < n_problems; p += blockDim.x)
+        if (cnt_p[p]) atomicAdd(&out[p], (unsigned long long)cnt_p[p]);
+}
+
+// Commit of a layer computed into buffer `cur`: its output list becomes the
+// operator.  Skipped after an error, so the last completed layer's operator
+// stays committed.
+__global__ void k_commit(Counters* ctr, int cur) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || ctr->err) return;
+    ctr->n_live = ctr->n_done;
+    ctr->cur = cur;
+    ctr->n_layers += 1;
+}
+
+// Sets the committed operator from the host (after a host-side commit).
+__global__ void k_set_live(Counters* ctr, long long n, int cur) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    ctr->n_live = (unsigned long long)n;
+    ctr->cur = cur;
 }
 
 }  // namespace orqa

@@ -50,9 +50,11 @@ __device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int
 // counted into their pass-0 fine bucket.
 // ---------------------------------------------------------------------------
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrList done, StrList active,
-                                                  long long cap, const __grid_constant__ RxRun run,
-                                                  Counters* ctr, int32_t* fcount, int fshift) {
+__global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, StrList active, long long cap,
+                                                  const __grid_constant__ RxRun run, Counters* ctr,
+                                                  int32_t* fcount, int fshift) {
+    if (block_aborted(ctr)) return;
+    const long long n = min((long long)ctr->n_live, cap);
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
     const unsigned long long dbits = Coef<T>::threshold(run);
@@ -83,18 +85,20 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrL
         if (to_done || act) {
             const long long slot = to_done ? sd : sa;
             StrList dst = to_done ? done : active;
+            const unsigned pid = src.pid ? src.pid[i] : 0u;
             load_plane<W>(src.x, i, x);
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z);
                 reinterpret_cast<T*>(dst.c)[slot] = c;
+                if (dst.pid) dst.pid[slot] = (uint16_t)pid;
             } else {
-                ctr->overflow = 1u;
+                atomicOr(&ctr->err, ERR_OVERFLOW);
             }
             if (act) {
                 int pos[CHUNK_BITS], np, idx;
                 bool more;
-                const uint64_t h = unit_key_hash<W>(x, z, run.mask, 0, pos, np, idx, more);
+                const uint64_t h = unit_key_hash<W>(x, z, run.mask, 0, pos, np, idx, more, pid);
                 const int rk = atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
                 if (slot < cap) {
                     active.h[slot] = h;
@@ -103,8 +107,27 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, long long n, StrL
             }
         }
         const unsigned nd = __popc(__ballot_sync(FULL_MASK, live && !act && !keep));
-        if ((threadIdx.x & 31) == 0 && nd) atomicAdd(&ctr->dropped, (unsigned long long)nd);
+        if ((threadIdx.x & 31) == 0 && nd) {
+            atomicAdd(&ctr->dropped, (unsigned long long)nd);
+            atomicAdd(&ctr->split_dropped, (unsigned long long)nd);
+        }
     }
+}
+
+// Pass bookkeeping between the kernels of an X layer (one thread): the list
+// just written becomes the active list of the next pass.  With use_cond it
+// also sets the condition of the enclosing graph loop (another pass is
+// needed iff strings are active and no error was raised).
+__global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHandle cond, int use_cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long na = ctr->n_next;
+    ctr->n_active = na;
+    ctr->n_next = 0;
+    ctr->range_cursor = 0;
+    ctr->pass = first ? 0 : ctr->pass + 1;
+    const unsigned long long pk = ctr->n_done + na;
+    if (pk > ctr->peak) ctr->peak = pk;
+    if (use_cond) cudaGraphSetConditional(cond, (na > 0 && ctr->err == 0) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -142,7 +165,8 @@ __device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& t
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int32_t* counts, long long* offsets,
-                                                             long long* tile_sums) {
+                                                             long long* tile_sums, const Counters* ctr) {
+    if (block_aborted(ctr)) return;
     __shared__ int warp_tot[33];
     const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS], s = 0;
@@ -163,7 +187,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int32_t* coun
 
 // One block; n_tiles <= SCAN_TILE.  All counts fit in int (they sum to at
 // most the capacity, < 2^31).
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums, int n_tiles) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums, int n_tiles,
+                                                           const Counters* ctr) {
+    if (block_aborted(ctr)) return;
     __shared__ int warp_tot[33];
     const int t = threadIdx.x;
     int v[SCAN_ITEMS], s = 0;
@@ -192,7 +218,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums,
 // J = ceil(total / T).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, const long long* tile_sums,
                                                            const int32_t* counts, long long n,
-                                                           int32_t* range_start, long long T) {
+                                                           int32_t* range_start, long long T,
+                                                           const Counters* ctr) {
+    if (block_aborted(ctr)) return;
     const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
     const long long add = tile_sums[blockIdx.x];
     const long long total = tile_sums[SCAN_TILE];
@@ -267,8 +295,15 @@ __device__ __forceinline__ void load_record(const void* base, long long i, uint6
 constexpr int record_bytes(int W) { return W == 2 ? 64 : 32; }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n, int fshift,
-                                                        const long long* __restrict__ offsets, void* dst) {
+__global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long cap, int fshift,
+                                                        const long long* __restrict__ offsets, void* dst,
+                                                        int32_t* fcount, long long n_fine, Counters* ctr) {
+    if (block_aborted(ctr)) return;
+    const long long n = min((long long)ctr->n_active, cap);
+    // the counts were consumed by the scan; clear them for the next pass
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < n_fine;
+         b += (long long)gridDim.x * blockDim.x)
+        fcount[b] = 0;
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
     for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x; base < n;
          base += stride) {
@@ -291,6 +326,10 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long n
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
             if (slot[k] < 0) continue;
+            if (slot[k] >= cap) {  // only reachable after an undetected count error; never write past the records
+                atomicOr(&ctr->err, ERR_OVERFLOW);
+                continue;
+            }
             uint64_t x[W], z[W];
             load_plane<W>(src.x, i, x);
             load_plane<W>(src.z, i, z);
@@ -330,9 +369,11 @@ struct LocalSmem {
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
     int16_t rep_uid[LB_MAX];
     int16_t u_rep[LB_MAX];
+    uint16_t spid[LB_MAX];      // problem index of each string
     uint16_t list1[LB_WARPS][LB_LIST];
     uint16_t list2[LB_WARPS][LB_LIST];
-    uint8_t hq[LB_RU];          // qubit of the current level, per unit
+    T hcs[LB_RU];               // cos and sin of the current level's gate, per unit
+    T hsn[LB_RU];
     uint8_t s_idx[LB_MAX];
     int blk_delta[MAX_QUBITS];
     int warp_tot[33];
@@ -341,6 +382,7 @@ struct LocalSmem {
     long long range[2];
     int bucket_range[3];
     int n_units;
+    int claim;
 };
 
 __device__ __forceinline__ unsigned level_mask(int j) {
@@ -381,34 +423,47 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     return ((uint64_t)hi << 32) | lo;
 }
 
+// Persistent: each CTA claims ranges from a device cursor until none is
+// left, so the grid can be fixed (as in a captured graph) and uneven ranges
+// balance across CTAs.  The number of ranges J = ceil(total / range_target)
+// and the pass index are read from the device.  A sub-range holds at most
+// sub_max <= LB_MAX strings (the load of the shared-memory hash table is at
+// most sub_max / LB_TABLE).
 template <int W, typename T>
 __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
     const void* bk, const long long* __restrict__ offsets, const int32_t* __restrict__ range_start,
-    const __grid_constant__ RxRun run,
-    int pass, StrList done, StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift,
-    unsigned long long* pop_delta) {
+    long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
+    StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift, unsigned long long* pop_delta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LocalSmem<W, T>& S = *reinterpret_cast<LocalSmem<W, T>*>(smem_raw);
+    if (block_aborted(ctr)) return;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const unsigned long long dbits = Coef<T>::threshold(run);
+    const int pass = ctr->pass;
+    const long long J = (offsets[n_fine] + range_target - 1) / range_target;
 
-    // ---- range: whole buckets whose start lies in [j*T, (j+1)*T) (found by
-    // the scan), processed in sub-ranges of whole buckets that fit in shared
-    // memory
-    if (tid < 2) S.bucket_range[tid] = range_start[blockIdx.x + tid];
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) S.blk_delta[t] = 0;
-    __syncthreads();
     unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
+    for (;;) {  // block-uniform
+    if (tid == 0) S.claim = (int)atomicAdd(&ctr->range_cursor, 1u);
+    __syncthreads();
+    const int rj = S.claim;
+    if (rj >= J) break;
+    // ---- range rj: whole buckets whose start lies in [rj*T, (rj+1)*T)
+    // (found by the scan), processed in sub-ranges of whole buckets that fit
+    // in shared memory
+    if (tid < 2) S.bucket_range[tid] = range_start[rj + tid];
+    __syncthreads();
     const int b_end = S.bucket_range[1];
     for (int b_lo = S.bucket_range[0]; b_lo < b_end;) {  // block-uniform
     __syncthreads();  // everyone has read the previous sub-range's bounds
     if (tid == 0) {
-        // last bucket boundary b <= b_end with offsets[b] - offsets[b_lo] <= LB_MAX
+        // last bucket boundary b <= b_end with offsets[b] - offsets[b_lo] <= sub_max
         const long long base = offsets[b_lo];
         int lo = b_lo, hi = b_end;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] - base <= LB_MAX)
+            if (offsets[mid] - base <= sub_max)
                 lo = mid;
             else
                 hi = mid - 1;
@@ -422,8 +477,8 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
     const long long s0 = S.range[0];
     const int m = (int)(S.range[1] - S.range[0]);
     const int b_next = S.bucket_range[2];
-    if (b_next == b_lo) {  // one bucket alone exceeds LB_MAX
-        if (tid == 0) atomicExch(&ctr->bucket_overflow, 1u);
+    if (b_next == b_lo) {  // one bucket alone exceeds sub_max
+        if (tid == 0) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
         break;
     }
     b_lo = b_next;
@@ -450,6 +505,7 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
             S.sz[w][i] = z[w];
         }
         S.sc[i] = c;
+        S.spid[i] = (uint16_t)pid_of(h);
         S.s_idx[i] = (uint8_t)idx;
         S.s_unit[i] = (int16_t)(h & (uint64_t)(LB_TABLE - 1));  // home slot, replaced below
     }
@@ -462,12 +518,13 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
             xb[w] = S.sx[w][i];
             z[w] = S.sz[w][i];
         }
+        const uint16_t pi = S.spid[i];
         int slot = S.s_unit[i];
         int rep = i;
         for (int probe = 0; probe < LB_TABLE; ++probe) {  // 2*LB_MAX slots: never full
             const int v = atomicCAS(&S.table[slot], -1, i);
             if (v == -1) break;
-            bool eq = true;
+            bool eq = S.spid[v] == pi;
 #pragma unroll
             for (int w = 0; w < W; ++w) eq = eq && (S.sz[w][v] == z[w]) && (S.sx[w][v] == xb[w]);
             if (eq) {
@@ -516,10 +573,12 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
         int pos[CHUNK_BITS] = {0, 0, 0, 0, 0}, pos2[CHUNK_BITS] = {0, 0, 0, 0, 0};
         int np = 0, np2 = 0;
         bool more = false;
+        unsigned upid = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) z[w] = xb[w] = xn[w] = 0;
         if (own) {
             const int rep = S.u_rep[u];
+            upid = S.spid[rep];
             uint64_t f[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -561,7 +620,10 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 sgl = lo ^ hi;
                 dbl = lo & hi;
                 pop_before = __popc(o);
-                S.hq[ub + lane] = (uint8_t)pos[j];
+                T co, sn;
+                Coef<T>::rot(run, upid, pos[j], co, sn);
+                S.hcs[ub + lane] = co;
+                S.hsn[ub + lane] = sn;
             }
             unsigned tot;
             unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
@@ -579,9 +641,8 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 const int e = S.list1[wp][t];
                 const int ur = ub + (e >> 6), la = e & 31, lb = la | bit;
                 const bool y_side = (e & 32) != 0;
-                const int q = S.hq[ur];
                 const T v = S.dense[ur][y_side ? lb : la];
-                const T p1 = Coef<T>::mul(Coef<T>::cos_of(run, q), v), p2 = Coef<T>::mul(Coef<T>::sin_of(run, q), v);
+                const T p1 = Coef<T>::mul(S.hcs[ur], v), p2 = Coef<T>::mul(S.hsn[ur], v);
                 // sigma_z present: (cos c, sin c); sigma_y present: (-sin c, cos c)
                 const T na = y_side ? Coef<T>::negate(p2) : p1;
                 const T nb = y_side ? p1 : p2;
@@ -597,9 +658,8 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
             for (unsigned t = lane; t < n2; t += 32) {
                 const int e = S.list2[wp][t];
                 const int ur = ub + (e >> 5), la = e & 31, lb = la | bit;
-                const int q = S.hq[ur];
                 T na, nb;
-                pair_update(Coef<T>::cos_of(run, q), Coef<T>::sin_of(run, q), S.dense[ur][la], S.dense[ur][lb], na, nb);
+                pair_update(S.hcs[ur], S.hsn[ur], S.dense[ur][la], S.dense[ur][lb], na, nb);
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
                 S.dense[ur][la] = na;
@@ -658,6 +718,7 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
             const unsigned nof = __shfl_sync(FULL_MASK, noff, L);
             const int npl = __shfl_sync(FULL_MASK, np, L);
             const int np2l = __shfl_sync(FULL_MASK, np2, L);
+            const unsigned ppl = __shfl_sync(FULL_MASK, upid, L);
             uint64_t x[W], zz[W], x2[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -686,24 +747,26 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 // the next pass's chunk bits are cleared in its key (some of them
                 // may be this pass's bits just set)
                 for (int j = 0; j < np2l; ++j) clear_bit<W>(x2, p2l[j]);
-                h = hash_key<W>(zz, x2);
+                h = with_pid(hash_key<W>(zz, x2, ppl), ppl);
             }
             const int rk = mr ? atomicAdd(&fcount_next[fine_bucket(h, fshift)], 1) : 0;
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, zz);
                 reinterpret_cast<T*>(dst.c)[slot] = S.dense[ub + L][l];
+                if (dst.pid) dst.pid[slot] = (uint16_t)ppl;
                 if (mr) {
                     dst.h[slot] = h;
                     dst.rank[slot] = rk;
                 }
             } else {
-                ctr->overflow = 1u;
+                atomicOr(&ctr->err, ERR_OVERFLOW);
             }
         }
         __syncwarp();
     }
     __syncthreads();  // shared arrays are reused by the next sub-range
+    }
     }
     const unsigned nb = __reduce_add_sync(FULL_MASK, (unsigned)my_branch);
     const unsigned nd = __reduce_add_sync(FULL_MASK, (unsigned)my_drop);

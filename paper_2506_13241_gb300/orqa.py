@@ -26,8 +26,11 @@ ORQA_FLAG_FP32 = 4
 EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_set_operator_device",
             "orqa_apply_layer", "orqa_merge_truncate", "orqa_expect", "orqa_export", "orqa_stats",
             "orqa_profile_count", "orqa_profile", "orqa_profile_reset",
-            "orqa_last_error", "orqa_destroy", "orqa_expect_noalloc"]
+            "orqa_last_error", "orqa_destroy", "orqa_expect_noalloc",
+            "orqa_workspace_bytes_batch", "orqa_set_operator_batch", "orqa_apply_layer_batch",
+            "orqa_expect_batch", "orqa_problem_sizes", "orqa_export_batch"]
 ORQA_NOALLOC_MAX_STRINGS = 1 << 27
+ORQA_MAX_PROBLEMS = 4096
 
 
 class orqa_gate(ctypes.Structure):
@@ -38,7 +41,7 @@ class orqa_gate(ctypes.Structure):
 class orqa_config(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("flags", ctypes.c_int32), ("capacity", ctypes.c_int64),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("n_problems", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class orqa_stats_t(ctypes.Structure):
@@ -104,6 +107,20 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_destroy.argtypes = [vp]
         lib.orqa_expect_noalloc.restype = i32
         lib.orqa_expect_noalloc.argtypes = [i32, i64, vp, vp, dpp, vp]
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.orqa_workspace_bytes_batch.restype = ctypes.c_uint64
+        lib.orqa_workspace_bytes_batch.argtypes = [i32, i64, i32]
+        lib.orqa_set_operator_batch.restype = i32
+        lib.orqa_set_operator_batch.argtypes = [vp, i64, vp, vp, vp, vp]
+        lib.orqa_apply_layer_batch.restype = i32
+        lib.orqa_apply_layer_batch.argtypes = [vp, ctypes.POINTER(orqa_gate), i32, vp, dp, i64p]
+        lib.orqa_expect_batch.restype = i32
+        lib.orqa_expect_batch.argtypes = [vp, dpp]
+        lib.orqa_problem_sizes.restype = i32
+        lib.orqa_problem_sizes.argtypes = [vp, i64p]
+        lib.orqa_export_batch.restype = i32
+        lib.orqa_export_batch.argtypes = [vp, i64, u64p, u64p, dpp, i32p, i64p]
         _lib = lib
     return _lib
 
@@ -151,9 +168,13 @@ def orqa_workspace_bytes(n_qubits: int, capacity: int) -> int:
     return int(library().orqa_workspace_bytes(n_qubits, capacity))
 
 
+def orqa_workspace_bytes_batch(n_qubits: int, capacity: int, n_problems: int) -> int:
+    return int(library().orqa_workspace_bytes_batch(n_qubits, capacity, n_problems))
+
+
 def orqa_create(n_qubits: int, capacity: int, workspace_ptr: int, workspace_bytes: int,
-                stream_ptr: int = 0, flags: int = 0):
-    cfg = orqa_config(n_qubits, flags, capacity, workspace_ptr, workspace_bytes, stream_ptr)
+                stream_ptr: int = 0, flags: int = 0, n_problems: int = 0):
+    cfg = orqa_config(n_qubits, flags, capacity, workspace_ptr, workspace_bytes, stream_ptr, n_problems, 0)
     h = ctypes.c_void_p()
     st = library().orqa_create(ctypes.byref(cfg), ctypes.byref(h))
     if st != ORQA_OK:
@@ -172,6 +193,57 @@ def orqa_set_operator_device(ctx, x, z, c):
     """x, z: contiguous int64/uint64 torch tensors [N, W]; c: float64 [N]."""
     _check(ctx, library().orqa_set_operator_device(ctx, c.numel(), x.data_ptr(), z.data_ptr(),
                                                    c.data_ptr()))
+
+
+def orqa_set_operator_batch(ctx, x: np.ndarray, z: np.ndarray, c: np.ndarray, problem: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    problem = np.ascontiguousarray(problem, dtype=np.int32)
+    if len(problem) != len(c):
+        raise ValueError("one problem index per string")
+    _check(ctx, library().orqa_set_operator_batch(ctx, len(c), x.ctypes.data, z.ctypes.data, c.ctypes.data,
+                                                  problem.ctypes.data))
+
+
+def orqa_apply_layer_batch(ctx, gates, theta: np.ndarray, delta: float) -> int:
+    """theta: [n_problems, n_gates] angles (row p: problem p)."""
+    arr = gates if isinstance(gates, ctypes.Array) else gate_array(gates)
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    if theta.ndim != 2 or theta.shape[1] != len(arr):
+        raise ValueError("theta must be [n_problems, n_gates]")
+    n = ctypes.c_int64()
+    _check(ctx, library().orqa_apply_layer_batch(ctx, arr, len(arr), theta.ctypes.data, float(delta),
+                                                 ctypes.byref(n)))
+    return n.value
+
+
+def orqa_expect_batch(ctx, n_problems: int) -> np.ndarray:
+    out = np.zeros(n_problems, dtype=np.float64)
+    _check(ctx, library().orqa_expect_batch(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def orqa_problem_sizes(ctx, n_problems: int) -> np.ndarray:
+    out = np.zeros(n_problems, dtype=np.int64)
+    _check(ctx, library().orqa_problem_sizes(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out
+
+
+def orqa_export_batch(ctx, n_qubits: int):
+    W = words_per_plane(n_qubits)
+    n = orqa_stats(ctx)["n_strings"]
+    x = np.zeros((max(n, 1), W), dtype=np.uint64)
+    z = np.zeros((max(n, 1), W), dtype=np.uint64)
+    c = np.zeros(max(n, 1), dtype=np.float64)
+    p = np.zeros(max(n, 1), dtype=np.int32)
+    got = ctypes.c_int64()
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    _check(ctx, library().orqa_export_batch(ctx, n, x.ctypes.data_as(u64p), z.ctypes.data_as(u64p),
+                                            c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(got)))
+    k = got.value
+    return x[:k], z[:k], c[:k], p[:k]
 
 
 def orqa_apply_layer(ctx, gates, delta: float) -> int:
@@ -253,7 +325,7 @@ class Context:
     torch.cuda.Stream, default: the current stream)."""
 
     def __init__(self, n_qubits: int, capacity: int, stream=None, device=None, profile: bool = False,
-                 relative: bool = False, fp32: bool = False):
+                 relative: bool = False, fp32: bool = False, problems: int = 1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liborqa needs a CUDA device; none is available")
@@ -261,10 +333,11 @@ class Context:
         self.n_qubits = n_qubits
         self.W = words_per_plane(n_qubits)
         self.capacity = capacity
+        self.problems = problems
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            nbytes = orqa_workspace_bytes(n_qubits, capacity)
+            nbytes = orqa_workspace_bytes_batch(n_qubits, capacity, problems)
             if nbytes == 0:
                 raise ValueError("bad n_qubits / capacity")
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
@@ -272,7 +345,8 @@ class Context:
             aligned = (base + 255) // 256 * 256
             flags = ((ORQA_FLAG_PROFILE if profile else 0) | (ORQA_FLAG_RELATIVE if relative else 0) |
                      (ORQA_FLAG_FP32 if fp32 else 0))
-            self.ctx = orqa_create(n_qubits, capacity, aligned, nbytes, self.stream.cuda_stream, flags)
+            self.ctx = orqa_create(n_qubits, capacity, aligned, nbytes, self.stream.cuda_stream, flags,
+                                   problems if problems > 1 else 0)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:
@@ -295,6 +369,32 @@ class Context:
 
     def set_operator_device(self, x, z, c):
         orqa_set_operator_device(self.ctx, x, z, c)
+
+    def set_operator_batch(self, x, z, c, problem):
+        orqa_set_operator_batch(self.ctx, x, z, c, problem)
+
+    def set_labels_batch(self, terms_per_problem):
+        """terms_per_problem[p]: list of (label, coefficient) of problem p."""
+        labels, coefs, pids = [], [], []
+        for p, terms in enumerate(terms_per_problem):
+            for lab, c in terms:
+                labels.append(lab)
+                coefs.append(c)
+                pids.append(p)
+        x, z = strings_from_labels(labels, self.n_qubits)
+        self.set_operator_batch(x, z, np.array(coefs, dtype=np.float64), np.array(pids, dtype=np.int32))
+
+    def apply_layer_batch(self, gates, theta, delta: float = 0.0) -> int:
+        return orqa_apply_layer_batch(self.ctx, gates, theta, delta)
+
+    def expect_batch(self) -> np.ndarray:
+        return orqa_expect_batch(self.ctx, self.problems)
+
+    def problem_sizes(self) -> np.ndarray:
+        return orqa_problem_sizes(self.ctx, self.problems)
+
+    def export_batch(self):
+        return orqa_export_batch(self.ctx, self.n_qubits)
 
     def apply_layer(self, gates, delta: float = 0.0) -> int:
         return orqa_apply_layer(self.ctx, gates, delta)

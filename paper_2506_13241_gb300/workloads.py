@@ -197,3 +197,22 @@ def weighted_z_observable(n: int, edges, centre: int, weight: int):
     (ties broken by qubit index)."""
     order, _ = bfs_order(n, edges, centre)
     return z_label(n, order[:weight])
+
+
+def sweep_workload(n_theta: int = 32, steps: int = 10, delta: float = 1e-4, weights=(1, 3, 17)):
+    """Batched theta_h x observable sweep on the heavy-hex: n_theta angles
+    uniform in [0, pi/2] (both ends included) times Z-strings of the given
+    weights around qubit 62.  Problem p = i_theta * len(weights) + i_obs.
+    Returns n, edges, the layer template (angles of the X layer are
+    replaced per problem), the observables per problem, and theta[p]."""
+    n, edges = heavy_hex_eagle()
+    thetas = [0.5 * math.pi * k / (n_theta - 1) for k in range(n_theta)] if n_theta > 1 else [math.pi / 4]
+    obs = [weighted_z_observable(n, edges, 62, w) for w in weights]
+    problems, theta_p = [], []
+    for th in thetas:
+        for lab in obs:
+            problems.append([(lab, 1.0)])
+            theta_p.append(th)
+    return dict(name="sweep_%dx%d_t=%d_delta=%g" % (n_theta, len(weights), steps, delta), n=n, edges=edges,
+                layers=kicked_ising_layers(n, edges, math.pi / 4), problems=problems, theta=theta_p,
+                steps=steps, delta=delta, weights=list(weights))

@@ -55,6 +55,23 @@ def test_create_validates_config_before_touching_cuda(lib):
     assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_ENOMEM
     cfg = orqa.orqa_config(12, 8, 100, 4096, 1 << 30, 0)  # unknown flag bit
     assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, 0, 100, 4096, 1 << 30, 0, orqa.ORQA_MAX_PROBLEMS + 1, 0)  # too many problems
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, 0, 100, 4096, 1 << 30, 0, -1, 0)
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, orqa.ORQA_FLAG_RELATIVE, 100, 4096, 1 << 30, 0, 4, 0)  # relative + batched
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+    cfg = orqa.orqa_config(12, 0, 100, 4096, 1 << 30, 0, 4, 1)  # reserved field set
+    assert lib.orqa_create(ctypes.byref(cfg), ctypes.byref(h)) == orqa.ORQA_EINVAL
+
+
+def test_batch_workspace_sizes(lib):
+    one = orqa.orqa_workspace_bytes(127, 10000)
+    assert orqa.orqa_workspace_bytes_batch(127, 10000, 1) == one
+    assert orqa.orqa_workspace_bytes_batch(127, 10000, 0) == one
+    b2, b96 = orqa.orqa_workspace_bytes_batch(127, 10000, 2), orqa.orqa_workspace_bytes_batch(127, 10000, 96)
+    assert one < b2 < b96 and b96 % 256 == 0
+    assert orqa.orqa_workspace_bytes_batch(127, 10000, orqa.ORQA_MAX_PROBLEMS + 1) == 0
 
 
 def test_gate_array_marshalling():
@@ -62,7 +79,7 @@ def test_gate_array_marshalling():
     assert (arr[0].kind, arr[0].q0, arr[0].theta) == (orqa.ORQA_RX, 3, 0.5)
     assert (arr[1].kind, arr[1].q0, arr[1].q1) == (orqa.ORQA_RZZ, 1, 2)
     assert ctypes.sizeof(orqa.orqa_gate) == 24
-    assert ctypes.sizeof(orqa.orqa_config) == 40
+    assert ctypes.sizeof(orqa.orqa_config) == 48
     assert ctypes.sizeof(orqa.orqa_stats_t) == 72
 
 
