@@ -51,6 +51,10 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32: the precision form (FP32 coefficients, compensated pair updates)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="sweep workloads: pick the launch tuning by measurement before warm-up")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="sweep workloads: also time the plain FP64 path, one problem after another")
     return ap.parse_args(argv)
 
 
@@ -375,8 +379,198 @@ def workload_config(wl, precision="fp64"):
             "coefficients": precision, "l2": "flushed between timed steps"}
 
 
+# ---------------------------------------------------------------------------
+# Batched theta x observable sweep (one captured program for all problems)
+# ---------------------------------------------------------------------------
+
+def sweep_from_name(name: str):
+    """sweep[_n=<angles>][_t=<steps>][_delta=<d>]: angles uniform in
+    [0, pi/2] x Z-strings of weight 1, 3, 17 around qubit 62."""
+    n_theta, steps, delta = 32, 10, 1e-4
+    for part in name.split("_")[1:]:
+        k, v = part.split("=")
+        if k == "n":
+            n_theta = int(v)
+        elif k == "t":
+            steps = int(v)
+        elif k == "delta":
+            delta = float(v)
+    wl = W.sweep_workload(n_theta, steps, delta)
+    wl["name"] = name
+    return wl
+
+
+def sweep_inputs(wl):
+    import numpy as np
+    from paper_2506_13241_gb300 import orqa as B
+    labels, coefs, pids = [], [], []
+    for p, terms in enumerate(wl["problems"]):
+        for lab, c in terms:
+            labels.append(lab)
+            coefs.append(c)
+            pids.append(p)
+    x, z = B.strings_from_labels(labels, wl["n"])
+    return x, z, np.array(coefs, dtype=np.float64), np.array(pids, dtype=np.int32)
+
+
+def run_plain_sweep(wl, capacity):
+    """The plain FP64 path on the same problems, one after another (the
+    single-operator calls a user of the plain API makes)."""
+    import numpy as np
+    import torch
+    from paper_2506_13241_gb300 import orqa as B
+    n, steps, delta = wl["n"], wl["steps"], wl["delta"]
+    ctx = B.Context(n, capacity)
+    mags = np.zeros((steps, len(wl["problems"])))
+    updates = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p, terms in enumerate(wl["problems"]):
+        layers = [B.gate_array(layer) for layer in W.kicked_ising_layers(n, wl["edges"], wl["theta"][p])]
+        ctx.set_labels(terms)
+        for t in range(steps):
+            for layer in layers:
+                B.orqa_apply_layer(ctx.ctx, layer, delta)
+                updates += B.orqa_stats(ctx.ctx)["string_gate_updates"]
+            mags[t, p] = B.orqa_expect(ctx.ctx)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    del ctx
+    return {"seconds": secs, "updates": updates, "value": updates / secs, "unit": UNIT}, mags
+
+
+def sweep_launches(ctx_stats, wl, n_zz_launches):
+    """Kernel launches of one sweep step: the batched set_operator (merge: 4
+    kernels + commit) and the graph (per Trotter step: the ZZ launches and
+    their end kernel; the X layer's begin, split, pass-advance and end
+    kernels; 6 kernels per chunk pass; 2 expectation kernels)."""
+    steps = wl["steps"]
+    return 5 + steps * (n_zz_launches + 1 + 4 + 2) + 6 * int(ctx_stats["chunk_passes"])
+
+
+def run_sweep(args, wl, rank, world):
+    import numpy as np
+    import torch
+    from paper_2506_13241_gb300 import orqa as B
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n, P, steps, delta = wl["n"], len(wl["problems"]), wl["steps"], wl["delta"]
+    zz, xx = wl["layers"]
+    theta = np.array([[wl["theta"][p]] * len(xx) for p in range(P)])
+    fp32 = args.precision == "fp32"
+    capacity = int(args.capacity) if args.capacity else int(4e8)
+    ctx = B.Context(n, capacity, fp32=fp32, problems=P)
+    prog = ctx.program([(zz, False, None), (xx, True, theta)])
+    x, z, c, pid = sweep_inputs(wl)
+    stream = ctx.stream
+
+    def step():
+        B.orqa_set_operator_batch(ctx.ctx, x, z, c, pid)
+        return ctx.run_program(prog, steps, delta)
+
+    tuned = None
+    if args.autotune:
+        B.orqa_set_operator_batch(ctx.ctx, x, z, c, pid)
+        best, best_ms = ctx.autotune(prog, steps, delta, trials=1)
+        tuned = {"tuning": best, "graph_ms": best_ms}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, updates, mags = 0.0, 0, None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mags = step()
+            e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        updates += ctx.stats()["string_gate_updates"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st = ctx.stats()
+    e2e_s = 0.0
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step()
+        e2e_s += time.perf_counter() - t0
+    e2e_steps = max(1, min(args.steps, 2))
+    sizes = ctx.problem_sizes()
+    # kernel table of the same evolution, host-driven with per-launch events
+    pctx = B.Context(n, capacity, fp32=fp32, problems=P, profile=True)
+    B.orqa_set_operator_batch(pctx.ctx, x, z, c, pid)
+    zza, xxa = B.gate_array(zz), B.gate_array(xx)
+    for _ in range(steps):
+        B.orqa_apply_layer(pctx.ctx, zza, delta)
+        B.orqa_apply_layer_batch(pctx.ctx, xxa, theta, delta)
+        pctx.expect_batch()
+    prof = pctx.profile()
+    del pctx
+    n_zz = 1  # the kicked-Ising ZZ layer is one Clifford set: one closed-form launch
+    res = dict(total_ms=total_ms, updates=updates, mags=mags, clocks=clk, prof=prof, e2e_s=e2e_s,
+               e2e_updates=updates / args.steps * e2e_steps, stats=st, sizes=sizes, tuned=tuned,
+               launches=sweep_launches(st, wl, n_zz) * args.steps,
+               h2d=x.nbytes + z.nbytes + c.nbytes + pid.nbytes, d2h=steps * P * 8 + 64)
+    del ctx
+    return res
+
+
+def main_sweep(args, world, rank):
+    import numpy as np
+    if world > 1:
+        raise SystemExit("sweep workloads run on one GPU (one batched context)")
+    wl = sweep_from_name(args.workload)
+    from paper_2506_13241_gb300 import build
+    if rank == 0:
+        build.build()
+    res = run_sweep(args, wl, rank, world)
+    secs = res["total_ms"] * 1e-3
+    value = res["updates"] * world / secs
+    P = len(wl["problems"])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "lattice": "heavy-hex 127", "problems": P,
+                       "theta_x": "%d values uniform in [0, pi/2]" % (P // len(wl["weights"])),
+                       "observables": "Z-strings of weight %s around qubit 62" % wl["weights"],
+                       "time_steps": wl["steps"], "delta": wl["delta"],
+                       "truncation": "absolute |c| < delta after every X gate",
+                       "coefficients": args.precision, "execution": "one captured CUDA graph per step",
+                       "l2": "flushed between timed steps"},
+            "roofline": roofline_entry(res["prof"], 1),
+            "e2e": {"value": res["e2e_updates"] * world / res["e2e_s"], "unit": UNIT,
+                    "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "peak_strings": res["stats"]["last_layer_peak"], "chunk_passes_per_step": res["stats"]["chunk_passes"],
+            "final_sizes": {"total": int(res["sizes"].sum()), "max": int(res["sizes"].max())}}
+    if res["tuned"]:
+        line["autotune"] = res["tuned"]
+    if args.compare_plain:
+        plain, pm = run_plain_sweep(wl, int(6e7))
+        line["plain_fp64_sequential"] = plain
+        line["speedup_vs_plain_fp64"] = value / plain["value"]
+        diff = np.abs(np.asarray(res["mags"]) - pm)
+        line["magnetization_error_vs_plain_fp64"] = {"max_abs": float(diff.max()),
+                                                     "per_step_max": [float(v) for v in diff.max(axis=1)]}
+    print(json.dumps(line))
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload.startswith("sweep") and args.impl != "reference":
+        return main_sweep(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
     wl = W.workload(args.workload)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

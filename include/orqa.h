@@ -238,6 +238,65 @@ orqa_status orqa_problem_sizes(orqa_ctx* ctx, int64_t* out);
 orqa_status orqa_export_batch(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c,
                               int32_t* problem, int64_t* n_out);
 
+/* Captured programs.  A program is a sequence of layers repeated `repeat`
+ * times, for example the two layers of one kicked-Ising Trotter step
+ * repeated for t steps.  orqa_run_program applies it as ONE CUDA graph
+ * launch on the context's stream: every layer, every chunk pass of an X
+ * layer (a device-side loop: a conditional graph node re-runs the pass
+ * while strings remain active) and every requested expectation runs on the
+ * device with no host round trip.  The result is the one of the same layers
+ * applied with orqa_apply_layer(_batch), bit for bit.  The graph is captured
+ * on the first run and replayed while the program, delta, the tuning and the
+ * operator's buffer are unchanged.  Not available with ORQA_FLAG_RELATIVE. */
+typedef struct {
+    const orqa_gate* gates;   /* one layer, as for orqa_apply_layer */
+    int32_t n_gates;
+    int32_t expect_after;     /* 1: evaluate <0|O|0> (every problem) after this layer */
+    const double* theta;      /* batched ORQA_RX layers: n_problems rows of n_gates
+                                 angles (as for orqa_apply_layer_batch), or NULL */
+} orqa_layer_desc;
+
+/* Runs the program.  expect_out: HOST array of n_expect_out doubles that
+ * receives, in order, the P values of every expect_after layer of every
+ * repetition (P = n_problems, 1 for a plain context); EINVAL if it is too
+ * short or the program asks for more than 65536 values.  On an error inside
+ * the graph (capacity, a bounded wait) the call returns that status, the
+ * context holds the operator after the last completed layer, and the
+ * values not yet computed are NaN. */
+orqa_status orqa_run_program(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t n_layers,
+                             int32_t repeat, double delta, double* expect_out, int64_t n_expect_out);
+
+/* Launch parameters of the X-layer pipeline.  Every setting gives the same
+ * result; they trade occupancy, scatter locality and shared-memory hash
+ * load.
+ *   range_target   strings per unit-kernel CTA range (tile), 128..4096
+ *   sub_max        most strings one shared-memory sub-range holds, 256..512;
+ *                  the shared hash table has 1024 slots, so its load is at
+ *                  most sub_max / 1024
+ *   bucket_density strings per fine bucket at full capacity (8, 16 or 32): the
+ *                  number of hash bits that partition the strings
+ *   grid_per_sm    CTAs per SM of the streaming kernels, 1..32 */
+typedef struct {
+    int32_t range_target;
+    int32_t sub_max;
+    int32_t bucket_density;
+    int32_t grid_per_sm;
+} orqa_tuning;
+
+orqa_status orqa_get_tuning(orqa_ctx* ctx, orqa_tuning* out);
+orqa_status orqa_set_tuning(orqa_ctx* ctx, const orqa_tuning* in);
+
+/* Picks the tuning for a program by measurement: starting from the current
+ * tuning, each parameter in turn is set to each of its candidate values
+ * (the others held), the program is run `trials` times from the current
+ * operator (restored before every run) and timed with CUDA events around
+ * the graph launch, and the fastest value is kept.  The best tuning is left
+ * set, *best_ms (may be NULL) receives its time, and the operator is
+ * restored.  The operator must fit the host memory of one export. */
+orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t n_layers,
+                          int32_t repeat, double delta, int32_t trials, orqa_tuning* best,
+                          double* best_ms);
+
 /* Largest operator orqa_expect_noalloc accepts (2^27 strings). */
 #define ORQA_NOALLOC_MAX_STRINGS 134217728LL
 

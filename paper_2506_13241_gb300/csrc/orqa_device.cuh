@@ -32,6 +32,10 @@ constexpr unsigned ERR_OVERFLOW = 1u;         // an append would have exceeded c
 constexpr unsigned ERR_TIMEOUT = 2u;          // a bounded spin-wait gave up
 constexpr unsigned ERR_TABLE_FULL = 4u;       // the merge hash table had no free slot
 constexpr unsigned ERR_BUCKET_OVERFLOW = 8u;  // a CTA range exceeded its shared-memory capacity
+constexpr unsigned ERR_PASS_LIMIT = 16u;      // an X layer needed more chunk passes than qubits allow
+// A run of at most 128 X gates needs at most ceil(128 / CHUNK_BITS) = 26
+// chunk passes; the pass loops stop (with ERR_PASS_LIMIT) beyond this.
+constexpr int MAX_PASSES = 32;
 
 // Device counters.  The fields before `err` describe the layer (or merge)
 // in progress and are cleared when it starts.  `err` is sticky within a
@@ -50,6 +54,7 @@ struct Counters {
     unsigned long long n_active;     // strings in the active list of the current pass
     unsigned long long split_dropped;  // strings the entry split dropped
     unsigned long long peak;         // largest output + active count seen in the layer
+    unsigned long long n_in;         // |O| entering the layer (captured programs)
     unsigned int range_cursor;       // next CTA range of the unit kernel
     int pass;                        // chunk pass in progress
     unsigned int err;                // ERR_* bits
@@ -67,11 +72,25 @@ __device__ __forceinline__ bool block_aborted(const Counters* ctr) {
     return __syncthreads_or(threadIdx.x == 0 && *(const volatile unsigned*)&ctr->err != 0u) != 0;
 }
 
+// Totals of a captured program, accumulated on the device layer by layer.
+struct ProgramStats {
+    unsigned long long updates;      // sum over gates of |O| before the gate
+    unsigned long long peak;         // largest intermediate set
+    unsigned long long branch_events;
+    unsigned long long dropped;
+    unsigned long long pairs_one;
+    unsigned long long pairs_two;
+    unsigned long long passes;       // chunk passes of all X layers
+    unsigned long long x_layers;     // X layers completed
+};
+
 // Per-problem rotation table of a batched X layer: entry p * MAX_QUBITS + q
-// holds (cos, sin) of problem p's angle on qubit q.
+// holds (cos, sin) of problem p's angle on qubit q; the FP32 table holds
+// them as float pairs (cos_hi, sin_hi, cos_lo, sin_lo) with hi + lo the
+// FP64 value to about 2^-48.
 struct RotTable {
     const double2* f64;
-    const float2* f32;
+    const float4* f32;
 };
 
 // Per-layer parameters of a run of X rotations (strictly ascending qubits).
@@ -84,8 +103,26 @@ struct RxRun {
     RotTable tab;            // batched contexts: per-problem angles (else null)
     double cs[MAX_QUBITS];   // cos(theta_q), exact at Clifford angles
     double sn[MAX_QUBITS];   // sin(theta_q)
-    float csf[MAX_QUBITS];   // the same, rounded to FP32 on the host
+    float csf[MAX_QUBITS];   // the same as float pairs hi + lo (FP32 form)
     float snf[MAX_QUBITS];
+    float cslf[MAX_QUBITS];
+    float snlf[MAX_QUBITS];
+};
+
+// cos and sin of one gate in the coefficient type's arithmetic: FP64
+// values, or (FP32 form) float pairs hi + lo that carry the FP64 value, so
+// the rounding of cos and sin to float does not bias every product.
+template <typename T>
+struct Rot;
+
+template <>
+struct Rot<double> {
+    double c, s;
+};
+
+template <>
+struct Rot<float> {
+    float c, s, cl, sl;
 };
 
 // ZZ layer parameters.  Edges of one Clifford mode form a set; a set is
@@ -416,15 +453,12 @@ struct Coef<double> {
     __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits64; }
     __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
     // (cos, sin) of problem p's angle on qubit q
-    __device__ static void rot(const RxRun& r, unsigned p, int q, double& c, double& s) {
+    __device__ static Rot<double> rot(const RxRun& r, unsigned p, int q) {
         if (r.tab.f64) {
             const double2 v = r.tab.f64[p * MAX_QUBITS + q];
-            c = v.x;
-            s = v.y;
-        } else {
-            c = r.cs[q];
-            s = r.sn[q];
+            return {v.x, v.y};
         }
+        return {r.cs[q], r.sn[q]};
     }
 };
 
@@ -436,15 +470,12 @@ struct Coef<float> {
     __device__ static float from_slot(unsigned long long b) { return __uint_as_float((unsigned)b); }
     __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits32; }
     __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
-    __device__ static void rot(const RxRun& r, unsigned p, int q, float& c, float& s) {
+    __device__ static Rot<float> rot(const RxRun& r, unsigned p, int q) {
         if (r.tab.f32) {
-            const float2 v = r.tab.f32[p * MAX_QUBITS + q];
-            c = v.x;
-            s = v.y;
-        } else {
-            c = r.csf[q];
-            s = r.snf[q];
+            const float4 v = r.tab.f32[p * MAX_QUBITS + q];
+            return {v.x, v.y, v.z, v.w};
         }
+        return {r.csf[q], r.snf[q], r.cslf[q], r.snlf[q]};
     }
 };
 
@@ -459,28 +490,47 @@ __device__ __forceinline__ bool nonzero_t(T v) {
     return Coef<T>::mag(v) != 0ull;
 }
 
-// a*b + c*d in FP32 with the compensated scheme Dot2 (Ogita, Rump, Oishi
-// 2005): exact products by FMA (TwoProduct), exact sum by TwoSum, and the
-// three error terms added before the final rounding.
-__device__ __forceinline__ float dot2f(float a, float b, float c, float d) {
+// a*b + c*d (+ a small correction `extra`) in FP32 with the compensated
+// scheme Dot2 (Ogita, Rump, Oishi 2005): exact products by FMA
+// (TwoProduct), exact sum by TwoSum, and the error terms added before the
+// final rounding.
+__device__ __forceinline__ float dot2f(float a, float b, float c, float d, float extra) {
     const float p = __fmul_rn(a, b), ep = __fmaf_rn(a, b, -p);
     const float q = __fmul_rn(c, d), eq = __fmaf_rn(c, d, -q);
     const float s = __fadd_rn(p, q);
     const float t = __fsub_rn(s, p);
     const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(s, t)), __fsub_rn(q, t));
-    return __fadd_rn(s, __fadd_rn(es, __fadd_rn(ep, eq)));
+    return __fadd_rn(s, __fadd_rn(es, __fadd_rn(__fadd_rn(ep, eq), extra)));
+}
+
+// (hi + lo) * v rounded once to float: TwoProduct of hi * v plus lo * v.
+__device__ __forceinline__ float mul_pair(float hi, float lo, float v) {
+    const float p = __fmul_rn(hi, v);
+    const float e = __fmaf_rn(hi, v, -p);
+    return __fadd_rn(p, __fmaf_rn(lo, v, e));
+}
+
+// One-member pair (Eq. update_rule with the partner absent): (cos v, sin v).
+__device__ __forceinline__ void one_member(const Rot<double>& r, double v, double& pc, double& ps) {
+    pc = __dmul_rn(r.c, v);
+    ps = __dmul_rn(r.s, v);
+}
+
+__device__ __forceinline__ void one_member(const Rot<float>& r, float v, float& pc, float& ps) {
+    pc = mul_pair(r.c, r.cl, v);
+    ps = mul_pair(r.s, r.sl, v);
 }
 
 // Pair update of Eq. (update_rule) with both members present:
 // (c_Z, c_Y) -> (cos c_Z - sin c_Y, cos c_Y + sin c_Z).
-__device__ __forceinline__ void pair_update(double co, double sn, double a, double b, double& na, double& nb) {
-    na = __dsub_rn(__dmul_rn(co, a), __dmul_rn(sn, b));
-    nb = __dadd_rn(__dmul_rn(co, b), __dmul_rn(sn, a));
+__device__ __forceinline__ void pair_update(const Rot<double>& r, double a, double b, double& na, double& nb) {
+    na = __dsub_rn(__dmul_rn(r.c, a), __dmul_rn(r.s, b));
+    nb = __dadd_rn(__dmul_rn(r.c, b), __dmul_rn(r.s, a));
 }
 
-__device__ __forceinline__ void pair_update(float co, float sn, float a, float b, float& na, float& nb) {
-    na = dot2f(co, a, -sn, b);
-    nb = dot2f(co, b, sn, a);
+__device__ __forceinline__ void pair_update(const Rot<float>& r, float a, float b, float& na, float& nb) {
+    na = dot2f(r.c, a, -r.s, b, __fmaf_rn(r.cl, a, -__fmul_rn(r.sl, b)));
+    nb = dot2f(r.c, b, r.s, a, __fmaf_rn(r.cl, b, __fmul_rn(r.sl, a)));
 }
 
 }  // namespace orqa

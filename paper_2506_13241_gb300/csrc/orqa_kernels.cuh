@@ -410,6 +410,63 @@ __global__ void k_commit(Counters* ctr, int cur) {
     ctr->n_layers += 1;
 }
 
+// Start of an X layer inside a captured program: clears the layer counters
+// (not the error bits or the committed operator) and the per-qubit
+// population deltas, and records |O| entering the layer.
+__global__ void k_layer_begin(Counters* ctr, unsigned long long* pop_delta) {
+    const int t = threadIdx.x;
+    if (blockIdx.x != 0) return;
+    for (int q = t; q < MAX_QUBITS; q += blockDim.x) pop_delta[q] = 0ull;
+    if (t != 0) return;
+    ctr->n_done = ctr->n_next = ctr->n_units = ctr->unit_cursor = 0;
+    ctr->branch_events = ctr->dropped = ctr->pairs_one = ctr->pairs_two = 0;
+    ctr->n_active = ctr->split_dropped = ctr->peak = 0;
+    ctr->n_in = ctr->n_live;
+    ctr->range_cursor = 0;
+    ctr->pass = 0;
+}
+
+// End of an X layer inside a captured program: commits its output list
+// (buffer `cur`) and adds the layer to the program totals.  The updates are
+// the sum over the run's gates (ascending qubits of mask) of |O| before the
+// gate: |O| changes at gate q by the population delta recorded there, and
+// by the strings the entry split dropped at the first gate.
+__global__ void k_layer_end_x(Counters* ctr, int cur, uint64_t mask0, uint64_t mask1,
+                              const unsigned long long* pop_delta, ProgramStats* ps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || ctr->err) return;
+    unsigned long long pop = ctr->n_in, upd = 0;
+    bool first = true;
+    for (int w = 0; w < 2; ++w) {
+        for (uint64_t m = w ? mask1 : mask0; m; m &= m - 1) {
+            const int q = 64 * w + __ffsll((long long)m) - 1;
+            upd += pop;
+            pop += pop_delta[q];
+            if (first) pop -= ctr->split_dropped;
+            first = false;
+        }
+    }
+    ctr->n_live = ctr->n_done;
+    ctr->cur = cur;
+    ctr->n_layers += 1;
+    ps->updates += upd;
+    if (ctr->peak > ps->peak) ps->peak = ctr->peak;
+    ps->branch_events += ctr->branch_events;
+    ps->dropped += ctr->dropped;
+    ps->pairs_one += ctr->pairs_one;
+    ps->pairs_two += ctr->pairs_two;
+    ps->passes += (unsigned long long)ctr->pass;
+    ps->x_layers += 1;
+}
+
+// End of a ZZ layer inside a captured program (applied in place: |O| and
+// the buffer are unchanged).
+__global__ void k_layer_end_zz(Counters* ctr, int n_gates, ProgramStats* ps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || ctr->err) return;
+    ctr->n_layers += 1;
+    ps->updates += ctr->n_live * (unsigned long long)n_gates;
+    if (ctr->n_live > ps->peak) ps->peak = ctr->n_live;
+}
+
 // Sets the committed operator from the host (after a host-side commit).
 __global__ void k_set_live(Counters* ctr, long long n, int cur) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;

@@ -125,6 +125,7 @@ __global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHan
     ctr->n_next = 0;
     ctr->range_cursor = 0;
     ctr->pass = first ? 0 : ctr->pass + 1;
+    if (na > 0 && ctr->pass >= MAX_PASSES) atomicOr(&ctr->err, ERR_PASS_LIMIT);  // bounds the loop
     const unsigned long long pk = ctr->n_done + na;
     if (pk > ctr->peak) ctr->peak = pk;
     if (use_cond) cudaGraphSetConditional(cond, (na > 0 && ctr->err == 0) ? 1u : 0u);
@@ -372,8 +373,7 @@ struct LocalSmem {
     uint16_t spid[LB_MAX];      // problem index of each string
     uint16_t list1[LB_WARPS][LB_LIST];
     uint16_t list2[LB_WARPS][LB_LIST];
-    T hcs[LB_RU];               // cos and sin of the current level's gate, per unit
-    T hsn[LB_RU];
+    Rot<T> hrot[LB_RU];         // cos and sin of the current level's gate, per unit
     uint8_t s_idx[LB_MAX];
     int blk_delta[MAX_QUBITS];
     int warp_tot[33];
@@ -620,10 +620,7 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 sgl = lo ^ hi;
                 dbl = lo & hi;
                 pop_before = __popc(o);
-                T co, sn;
-                Coef<T>::rot(run, upid, pos[j], co, sn);
-                S.hcs[ub + lane] = co;
-                S.hsn[ub + lane] = sn;
+                S.hrot[ub + lane] = Coef<T>::rot(run, upid, pos[j]);
             }
             unsigned tot;
             unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
@@ -642,7 +639,8 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 const int ur = ub + (e >> 6), la = e & 31, lb = la | bit;
                 const bool y_side = (e & 32) != 0;
                 const T v = S.dense[ur][y_side ? lb : la];
-                const T p1 = Coef<T>::mul(S.hcs[ur], v), p2 = Coef<T>::mul(S.hsn[ur], v);
+                T p1, p2;
+                one_member(S.hrot[ur], v, p1, p2);
                 // sigma_z present: (cos c, sin c); sigma_y present: (-sin c, cos c)
                 const T na = y_side ? Coef<T>::negate(p2) : p1;
                 const T nb = y_side ? p1 : p2;
@@ -659,7 +657,7 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 const int e = S.list2[wp][t];
                 const int ur = ub + (e >> 5), la = e & 31, lb = la | bit;
                 T na, nb;
-                pair_update(S.hcs[ur], S.hsn[ur], S.dense[ur][la], S.dense[ur][lb], na, nb);
+                pair_update(S.hrot[ur], S.dense[ur][la], S.dense[ur][lb], na, nb);
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
                 S.dense[ur][la] = na;

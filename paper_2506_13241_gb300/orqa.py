@@ -28,7 +28,8 @@ EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_se
             "orqa_profile_count", "orqa_profile", "orqa_profile_reset",
             "orqa_last_error", "orqa_destroy", "orqa_expect_noalloc",
             "orqa_workspace_bytes_batch", "orqa_set_operator_batch", "orqa_apply_layer_batch",
-            "orqa_expect_batch", "orqa_problem_sizes", "orqa_export_batch"]
+            "orqa_expect_batch", "orqa_problem_sizes", "orqa_export_batch",
+            "orqa_run_program", "orqa_get_tuning", "orqa_set_tuning", "orqa_autotune"]
 ORQA_NOALLOC_MAX_STRINGS = 1 << 27
 ORQA_MAX_PROBLEMS = 4096
 
@@ -42,6 +43,16 @@ class orqa_config(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("flags", ctypes.c_int32), ("capacity", ctypes.c_int64),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("n_problems", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class orqa_layer_desc(ctypes.Structure):
+    _fields_ = [("gates", ctypes.POINTER(orqa_gate)), ("n_gates", ctypes.c_int32),
+                ("expect_after", ctypes.c_int32), ("theta", ctypes.c_void_p)]
+
+
+class orqa_tuning(ctypes.Structure):
+    _fields_ = [("range_target", ctypes.c_int32), ("sub_max", ctypes.c_int32),
+                ("bucket_density", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32)]
 
 
 class orqa_stats_t(ctypes.Structure):
@@ -121,6 +132,16 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_problem_sizes.argtypes = [vp, i64p]
         lib.orqa_export_batch.restype = i32
         lib.orqa_export_batch.argtypes = [vp, i64, u64p, u64p, dpp, i32p, i64p]
+        ldp = ctypes.POINTER(orqa_layer_desc)
+        tp = ctypes.POINTER(orqa_tuning)
+        lib.orqa_run_program.restype = i32
+        lib.orqa_run_program.argtypes = [vp, ldp, i32, i32, dp, dpp, i64]
+        lib.orqa_get_tuning.restype = i32
+        lib.orqa_get_tuning.argtypes = [vp, tp]
+        lib.orqa_set_tuning.restype = i32
+        lib.orqa_set_tuning.argtypes = [vp, tp]
+        lib.orqa_autotune.restype = i32
+        lib.orqa_autotune.argtypes = [vp, ldp, i32, i32, dp, i32, tp, dpp]
         _lib = lib
     return _lib
 
@@ -244,6 +265,59 @@ def orqa_export_batch(ctx, n_qubits: int):
                                             p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(got)))
     k = got.value
     return x[:k], z[:k], c[:k], p[:k]
+
+
+class Program:
+    """A layer sequence for orqa_run_program: items (gates, expect_after,
+    theta) with theta an [n_problems, n_gates] array for batched X layers or
+    None.  Keeps the ctypes arrays alive."""
+
+    def __init__(self, layers, n_problems: int = 1):
+        self.gates = [g if isinstance(g, ctypes.Array) else gate_array(g) for g, _, _ in layers]
+        self.thetas = [None if t is None else np.ascontiguousarray(t, dtype=np.float64) for _, _, t in layers]
+        self.desc = (orqa_layer_desc * len(layers))()
+        self.n_expect_per_rep = 0
+        for k, (_, e, _) in enumerate(layers):
+            th = self.thetas[k]
+            if th is not None and th.shape != (n_problems, len(self.gates[k])):
+                raise ValueError("theta must be [n_problems, n_gates]")
+            self.desc[k].gates = ctypes.cast(self.gates[k], ctypes.POINTER(orqa_gate))
+            self.desc[k].n_gates = len(self.gates[k])
+            self.desc[k].expect_after = 1 if e else 0
+            self.desc[k].theta = th.ctypes.data if th is not None else None
+            self.n_expect_per_rep += 1 if e else 0
+        self.n_problems = n_problems
+
+
+def orqa_run_program(ctx, program: Program, repeat: int, delta: float) -> np.ndarray:
+    """Returns the expectation values as [repeat * n_expect_layers, n_problems]."""
+    n = program.n_expect_per_rep * repeat * program.n_problems
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    _check(ctx, library().orqa_run_program(ctx, program.desc, len(program.desc), repeat, float(delta),
+                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n))
+    return out[:n].reshape(-1, program.n_problems)
+
+
+def orqa_get_tuning(ctx) -> dict:
+    t = orqa_tuning()
+    _check(ctx, library().orqa_get_tuning(ctx, ctypes.byref(t)))
+    return {name: getattr(t, name) for name, _ in orqa_tuning._fields_}
+
+
+def orqa_set_tuning(ctx, **kw):
+    t = orqa_tuning()
+    _check(ctx, library().orqa_get_tuning(ctx, ctypes.byref(t)))
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    _check(ctx, library().orqa_set_tuning(ctx, ctypes.byref(t)))
+
+
+def orqa_autotune(ctx, program: Program, repeat: int, delta: float, trials: int = 2):
+    t = orqa_tuning()
+    ms = ctypes.c_double()
+    _check(ctx, library().orqa_autotune(ctx, program.desc, len(program.desc), repeat, float(delta), trials,
+                                        ctypes.byref(t), ctypes.byref(ms)))
+    return {name: getattr(t, name) for name, _ in orqa_tuning._fields_}, ms.value
 
 
 def orqa_apply_layer(ctx, gates, delta: float) -> int:
@@ -395,6 +469,21 @@ class Context:
 
     def export_batch(self):
         return orqa_export_batch(self.ctx, self.n_qubits)
+
+    def program(self, layers) -> Program:
+        return Program(layers, self.problems)
+
+    def run_program(self, program: Program, repeat: int, delta: float = 0.0) -> np.ndarray:
+        return orqa_run_program(self.ctx, program, repeat, delta)
+
+    def tuning(self) -> dict:
+        return orqa_get_tuning(self.ctx)
+
+    def set_tuning(self, **kw):
+        orqa_set_tuning(self.ctx, **kw)
+
+    def autotune(self, program: Program, repeat: int, delta: float = 0.0, trials: int = 2):
+        return orqa_autotune(self.ctx, program, repeat, delta, trials)
 
     def apply_layer(self, gates, delta: float = 0.0) -> int:
         return orqa_apply_layer(self.ctx, gates, delta)

@@ -81,6 +81,8 @@ def test_gate_array_marshalling():
     assert ctypes.sizeof(orqa.orqa_gate) == 24
     assert ctypes.sizeof(orqa.orqa_config) == 48
     assert ctypes.sizeof(orqa.orqa_stats_t) == 72
+    assert ctypes.sizeof(orqa.orqa_layer_desc) == 24
+    assert ctypes.sizeof(orqa.orqa_tuning) == 16
 
 
 def test_label_encoding_matches_paper_codes():
