@@ -168,6 +168,17 @@ orqa_status orqa_set_operator_device(orqa_ctx* ctx, int64_t n, const uint64_t* x
 orqa_status orqa_apply_layer(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_gates,
                              double delta, int64_t* n_live_out);
 
+/* Applies one rotation exp(-i theta/2 sigma_J) about a general Pauli string
+ * J given as HOST planes xj, zj (W words each, the string encoding above;
+ * not the identity, no qubit >= n_qubits), then merges duplicates and drops
+ * c == 0 and |c| < delta (relative: |c| <= delta * max|c|): one gate of
+ * Algorithm 1 for any sigma_J (Eq. update_rule).  A string P that
+ * anticommutes with J becomes cos(theta) P plus i^(1+B(J,P)) sin(theta)
+ * sigma_{J xor P}, where sigma_J sigma_P = i^B(J,P) sigma_{J xor P}.
+ * Generators need not commute with each other, so this call takes one gate. */
+orqa_status orqa_apply_pauli_rotation(orqa_ctx* ctx, const uint64_t* xj, const uint64_t* zj,
+                                      double theta, double delta, int64_t* n_live_out);
+
 /* Merges duplicate strings (sums their coefficients) and drops c == 0 and
  * |c| < delta: the insert-or-add and truncate loops of Algorithm 1 applied
  * to the whole operator.  n_live_out (may be NULL) receives |O|. */
@@ -182,6 +193,19 @@ orqa_status orqa_expect(orqa_ctx* ctx, double* out);
  * ECAPACITY (nothing copied) if |O| > cap. */
 orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c,
                         int64_t* n_out);
+
+/* Pauli-string density D_t(x) of App. D: counts of the live strings (all
+ * problems of a batched context) by sign and by bin of |x| = |c| / max|c|.
+ * The n_bins bins are uniform in log10|x| over [log10_lo, 0]: with
+ * w = -log10_lo / n_bins, edge k is t_k = max|c| * 10^(log10_lo + k w)
+ * (formed in FP64; t_n_bins = max|c|), bin k holds t_k <= |c| < t_{k+1}
+ * (the last bin also |c| = max|c|), and an extra bin n_bins counts
+ * |c| < t_0.  counts (HOST, 2 * (n_bins + 1) int64): counts[s * (n_bins + 1)
+ * + k], s = 0 for c > 0 and 1 for c < 0.  max_abs_out (may be NULL)
+ * receives max|c|.  1 <= n_bins <= 256, -300 <= log10_lo < 0.
+ * Normalising counts by |O| and the bin width gives D_t. */
+orqa_status orqa_histogram(orqa_ctx* ctx, int32_t n_bins, double log10_lo, int64_t* counts,
+                           double* max_abs_out);
 
 /* Counters of the operator and of the last apply_layer call. */
 orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out);

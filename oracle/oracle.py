@@ -131,6 +131,28 @@ def rotation_cos_sin(theta: float):
     return c.value, s.value
 
 
+def histogram(coefs, n_bins: int, log10_lo: float):
+    """Pauli-string density D_t(x) of App. D as counts: x = c / max|c|, bins
+    uniform in log10|x| over [log10_lo, 0].  Reading (the paper gives no
+    binning): edge k is t_k = max|c| * 10**(log10_lo + k * w) with
+    w = -log10_lo / n_bins; bin k holds t_k <= |c| < t_{k+1}, the last bin
+    also |c| = max|c|; column n_bins counts |c| < t_0; row 0 is c > 0 and
+    row 1 is c < 0.  Returns (counts [2, n_bins + 1], max|c|)."""
+    c = np.asarray(coefs, dtype=np.float64)
+    counts = np.zeros((2, n_bins + 1), dtype=np.int64)
+    if c.size == 0:
+        return counts, 0.0
+    a = np.abs(c)
+    m = float(a.max())
+    w = -log10_lo / n_bins
+    edges = np.array([m * 10.0 ** (log10_lo + k * w) for k in range(n_bins)])
+    k = np.searchsorted(edges, a, side="right") - 1   # largest k with edges[k] <= |c|
+    k = np.where(k < 0, n_bins, np.minimum(k, n_bins - 1))
+    row = np.where(c > 0, 0, 1)
+    np.add.at(counts, (row, k), 1)
+    return counts, m
+
+
 class Oracle:
     """A Pauli-sum operator O = sum_I O_I sigma_I held by the C++ oracle."""
 

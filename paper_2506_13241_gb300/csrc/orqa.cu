@@ -799,6 +799,97 @@ orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
     return host_commit(ctx, dst, (long long)h.n_done);
 }
 
+// One rotation about a general Pauli string (see k_pauli_expand), then the
+// duplicate merge with truncation: the per-gate loop of Algorithm 1.
+template <int W, typename T>
+orqa_status apply_pauli_impl(orqa_ctx* ctx, const uint64_t* xj, const uint64_t* zj, double theta, double delta) {
+    PauliGen J{};
+    for (int w = 0; w < W; ++w) {
+        J.x[w] = xj[w];
+        J.z[w] = zj[w];
+    }
+    bool cl;
+    cos_sin(theta, &J.c, &J.s, &cl);
+    J.ch = (float)J.c;
+    J.sh = (float)J.s;
+    J.cl = (float)(J.c - (double)J.ch);
+    J.sl = (float)(J.s - (double)J.sh);
+    const long long n_in = ctx->n;
+    const int stage = (ctx->cur + 1) % 3, out = (ctx->cur + 2) % 3;
+    if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+    if (n_in > 0) {
+        k_pauli_expand<W, T><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], n_in, ctx->buf[stage],
+                                                                           ctx->cap, J, ctx->ctr);
+        LAUNCH_CHECK(ctx);
+    }
+    Counters h{};
+    orqa_status st = sync_counters(ctx, &h);
+    if (st != ORQA_OK) return st;
+    if ((st = check_flags(ctx, h, "pauli rotation")) != ORQA_OK) return st;
+    const unsigned long long branches = h.branch_events;
+    long long m = 0;
+    const double dabs = ctx->relative ? 0.0 : delta;
+    if ((st = merge_into<W, T, T>(ctx, ctx->buf[stage], (long long)h.n_done, out, dabs, &m)) != ORQA_OK) return st;
+    const long long dropped_merge = ctx->stats.dropped;
+    if ((st = host_commit(ctx, out, m)) != ORQA_OK) return st;
+    long long dropped_rel = 0;
+    if (ctx->relative) {
+        if ((st = truncate_relative<W, T>(ctx, delta, &dropped_rel)) != ORQA_OK) return st;
+        ctx->clean_delta = 0.0;
+    } else {
+        ctx->clean_delta = delta;
+    }
+    ctx->stats.last_layer_in = n_in;
+    ctx->stats.last_layer_peak = std::max(n_in, (long long)h.n_done);
+    ctx->stats.string_gate_updates = n_in;
+    ctx->stats.branch_events = (int64_t)branches;
+    ctx->stats.dropped = dropped_merge + dropped_rel;
+    ctx->stats.pair_updates_one = 0;
+    ctx->stats.pair_updates_two = 0;
+    ctx->stats.chunk_passes = 0;
+    return ORQA_OK;
+}
+
+// D_t(x) of the committed operator (k_histogram): the edges are
+// t_k = max|c| * 10^(log10_lo + k * w), w = -log10_lo / n_bins, formed on the
+// host in FP64, with t_n_bins = max|c|.
+template <int W, typename T>
+orqa_status histogram_impl(orqa_ctx* ctx, int n_bins, double log10_lo, int64_t* counts, double* max_out) {
+    const int nb2 = 2 * (n_bins + 1);
+    std::vector<unsigned long long> hc((size_t)nb2, 0ull);
+    double mval = 0.0;
+    if (ctx->n > 0) {
+        unsigned long long* mx = (unsigned long long*)ctx->scalar;
+        CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, 8, ctx->stream));
+        k_absmax<T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(reinterpret_cast<const T*>(ctx->buf[ctx->cur].c),
+                                                                    ctx->n, mx);
+        LAUNCH_CHECK(ctx);
+        unsigned long long mb = 0;
+        CUDA_TRY(ctx, cudaMemcpyAsync(&mb, mx, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        mval = from_mag<T>(mb);
+        const double w = -log10_lo / n_bins;
+        std::vector<unsigned long long> tb((size_t)n_bins + 1);
+        for (int k = 0; k < n_bins; ++k) tb[(size_t)k] = ge_bits<T>(mval * std::pow(10.0, log10_lo + k * w));
+        tb[(size_t)n_bins] = ge_bits<T>(mval);
+        // scratch: thresholds then counts, in the expectation partials
+        if ((size_t)(n_bins + 1 + nb2) > (size_t)EXPECT_BLOCKS) return fail(ctx, ORQA_EINVAL, "histogram: too many bins");
+        unsigned long long* d_tb = reinterpret_cast<unsigned long long*>(ctx->partials);
+        unsigned long long* d_cnt = d_tb + n_bins + 1;
+        CUDA_TRY(ctx, cudaMemcpyAsync(d_tb, tb.data(), tb.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_TRY(ctx, cudaMemsetAsync(d_cnt, 0, (size_t)nb2 * 8, ctx->stream));
+        if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+        k_histogram<T><<<grid_for(ctx, ctx->n), 256, (size_t)nb2 * 4, ctx->stream>>>(
+            reinterpret_cast<const T*>(ctx->buf[ctx->cur].c), ctx->cap, ctx->ctr, d_tb, n_bins, d_cnt);
+        LAUNCH_CHECK(ctx);
+        CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), d_cnt, (size_t)nb2 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    for (int k = 0; k < nb2; ++k) counts[k] = (int64_t)hc[(size_t)k];
+    if (max_out) *max_out = mval;
+    return ORQA_OK;
+}
+
 // A layer with relative truncation.  ZZ gates keep every |c|, so the max is
 // unchanged through a ZZ layer and one truncation after it equals one after
 // every gate.  X gates are applied one at a time: the gate with exact zeros
@@ -1120,6 +1211,29 @@ orqa_status orqa_apply_layer_batch(orqa_ctx* ctx, const orqa_gate* gates, int32_
     return apply_layer_impl(ctx, gates, n_gates, theta, delta, n_live_out);
 }
 
+orqa_status orqa_apply_pauli_rotation(orqa_ctx* ctx, const uint64_t* xj, const uint64_t* zj, double theta,
+                                      double delta, int64_t* n_live_out) {
+    if (!ctx) return ORQA_EINVAL;
+    if (!xj || !zj || !std::isfinite(theta) || !(delta >= 0.0) || std::isinf(delta))
+        return fail(ctx, ORQA_EINVAL, "apply_pauli_rotation: bad arguments");
+    uint64_t any = 0;
+    for (int w = 0; w < ctx->W; ++w) {
+        any |= xj[w] | zj[w];
+        const int hi = ctx->n_qubits - 64 * w;  // qubits held by word w
+        if (hi < 64) {
+            const uint64_t outside = hi <= 0 ? ~0ull : ~((1ull << hi) - 1ull);
+            if ((xj[w] | zj[w]) & outside) return fail(ctx, ORQA_EINVAL, "apply_pauli_rotation: J acts beyond n_qubits");
+        }
+    }
+    if (!any) return fail(ctx, ORQA_EINVAL, "apply_pauli_rotation: J is the identity");
+    orqa_status st = ORQA_DISPATCH(ctx, apply_pauli_impl, ctx, xj, zj, theta, delta);
+    if (st != ORQA_OK) return st;
+    ctx->stats.n_strings = ctx->n;
+    if (n_live_out) *n_live_out = ctx->n;
+    ctx->err.clear();
+    return ORQA_OK;
+}
+
 orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out) {
     if (!ctx) return ORQA_EINVAL;
     if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "merge_truncate: bad delta");
@@ -1153,6 +1267,13 @@ orqa_status orqa_expect(orqa_ctx* ctx, double* out) {
 orqa_status orqa_expect_batch(orqa_ctx* ctx, double* out) {
     if (!ctx || !out) return ORQA_EINVAL;
     return ORQA_DISPATCH(ctx, expect_impl, ctx, out);
+}
+
+orqa_status orqa_histogram(orqa_ctx* ctx, int32_t n_bins, double log10_lo, int64_t* counts, double* max_abs_out) {
+    if (!ctx || !counts) return ORQA_EINVAL;
+    if (n_bins < 1 || n_bins > 256 || !(log10_lo < 0.0) || !std::isfinite(log10_lo) || log10_lo < -300.0)
+        return fail(ctx, ORQA_EINVAL, "histogram: need 1 <= n_bins <= 256 and -300 <= log10_lo < 0");
+    return ORQA_DISPATCH(ctx, histogram_impl, ctx, n_bins, log10_lo, counts, max_abs_out);
 }
 
 orqa_status orqa_problem_sizes(orqa_ctx* ctx, int64_t* out) {

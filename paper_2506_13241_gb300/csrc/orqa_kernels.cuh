@@ -410,6 +410,157 @@ __global__ void k_commit(Counters* ctr, int cur) {
     ctr->n_layers += 1;
 }
 
+// ---------------------------------------------------------------------------
+// Rotation about a general Pauli string J (Eq. update_rule for any sigma_J).
+// U^dagger P U for U = exp(-i theta J / 2) is P when P commutes with J and
+// cos(theta) P + i sin(theta) J P otherwise, with J P = i^B(J,P) sigma_{J xor P}
+// and B odd, so the child's factor is i^(1 + B): -1 for B = 1, +1 for B = 3.
+// B(J, P) mod 4 is counted per qubit from the single-qubit products (XY, YZ,
+// ZX give +1; XZ, YX, ZY give -1).  Each string writes itself (cos c) and,
+// if it anticommutes, its child (+-sin c) to a staging list; the duplicate
+// merge then sums the at most two terms of every string and truncates.
+// ---------------------------------------------------------------------------
+struct PauliGen {
+    uint64_t x[2], z[2];     // J as planes
+    double c, s;             // cos(theta), sin(theta), exact at Clifford angles
+    float ch, sh, cl, sl;    // the same as float pairs hi + lo (FP32 form)
+};
+
+template <int W>
+__device__ __forceinline__ int phase_exponent_jp(const PauliGen& J, const uint64_t (&x)[W], const uint64_t (&z)[W]) {
+    int plus = 0, minus = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint64_t jx = J.x[w] & ~J.z[w], jy = J.x[w] & J.z[w], jz = ~J.x[w] & J.z[w];
+        const uint64_t px = x[w] & ~z[w], py = x[w] & z[w], pz = ~x[w] & z[w];
+        plus += __popcll((jx & py) | (jy & pz) | (jz & px));
+        minus += __popcll((jx & pz) | (jy & px) | (jz & py));
+    }
+    return (plus - minus) & 3;
+}
+
+template <typename T>
+__device__ __forceinline__ void pauli_products(const PauliGen& J, T v, T& pc, T& ps);
+
+template <>
+__device__ __forceinline__ void pauli_products<double>(const PauliGen& J, double v, double& pc, double& ps) {
+    pc = __dmul_rn(J.c, v);
+    ps = __dmul_rn(J.s, v);
+}
+
+template <>
+__device__ __forceinline__ void pauli_products<float>(const PauliGen& J, float v, float& pc, float& ps) {
+    pc = mul_pair(J.ch, J.cl, v);
+    ps = mul_pair(J.sh, J.sl, v);
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_pauli_expand(StrList src, long long n, StrList dst, long long cap,
+                                                      const __grid_constant__ PauliGen J, Counters* ctr) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_round = (n + 31) & ~31ll;
+    const int lane = threadIdx.x & 31;
+    const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        uint64_t x[W], z[W];
+        T c = 0;
+        unsigned anti = 0, pid = 0;
+        const bool live = i < n;
+        if (live) {
+            load_plane<W>(src.x, i, x);
+            load_plane<W>(src.z, i, z);
+            c = sc[i];
+            if (src.pid) pid = src.pid[i];
+#pragma unroll
+            for (int w = 0; w < W; ++w) anti ^= (unsigned)__popcll((x[w] & J.z[w]) ^ (z[w] & J.x[w]));
+            anti &= 1u;
+        }
+        const unsigned cnt = live ? 1u + anti : 0u;
+        unsigned incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL_MASK, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const unsigned total = __shfl_sync(FULL_MASK, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && total) base = atomicAdd(&ctr->n_done, (unsigned long long)total);
+        base = __shfl_sync(FULL_MASK, base, 31);
+        const unsigned nb = __popc(__ballot_sync(FULL_MASK, anti != 0));
+        if (lane == 0 && nb) atomicAdd(&ctr->branch_events, (unsigned long long)nb);
+        if (!live) continue;
+        long long slot = (long long)(base + incl - cnt);
+        T keep = c, child = 0;
+        if (anti) {
+            T ps;
+            pauli_products<T>(J, c, keep, ps);
+            child = (phase_exponent_jp<W>(J, x, z) == 1) ? Coef<T>::negate(ps) : ps;
+        }
+        if (slot + (long long)cnt > cap) {
+            atomicOr(&ctr->err, ERR_OVERFLOW);
+            continue;
+        }
+        store_plane<W>(dst.x, slot, x);
+        store_plane<W>(dst.z, slot, z);
+        reinterpret_cast<T*>(dst.c)[slot] = keep;
+        if (dst.pid) dst.pid[slot] = (uint16_t)pid;
+        if (anti) {
+            ++slot;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                x[w] ^= J.x[w];
+                z[w] ^= J.z[w];
+            }
+            store_plane<W>(dst.x, slot, x);
+            store_plane<W>(dst.z, slot, z);
+            reinterpret_cast<T*>(dst.c)[slot] = child;
+            if (dst.pid) dst.pid[slot] = (uint16_t)pid;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pauli-string density D_t(x) (App. D): counts of the live strings by sign
+// and by bin of |x| = |c| / max|c|.  tbits[k] (k = 0..n_bins) are the
+// magnitude bits, in the stored type, of the bin edges t_k = max * e_k
+// (ascending, t_n_bins = max); bin k holds t_k <= |c| < t_{k+1} (the last
+// bin also |c| = max), and bin n_bins counts |c| < t_0.  counts[s * (n_bins
+// + 1) + k] with s = 0 for c > 0 and s = 1 for c < 0.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_histogram(const T* c, long long cap, const Counters* ctr,
+                                                   const unsigned long long* tbits, int n_bins,
+                                                   unsigned long long* counts) {
+    extern __shared__ unsigned hist_s[];
+    const int nb2 = 2 * (n_bins + 1);
+    for (int k = threadIdx.x; k < nb2; k += blockDim.x) hist_s[k] = 0u;
+    __syncthreads();
+    const long long n = min((long long)ctr->n_live, cap);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T v = c[i];
+        const unsigned long long m = Coef<T>::mag(v);
+        int bin;
+        if (m < tbits[0]) {
+            bin = n_bins;
+        } else {  // largest k <= n_bins - 1 with tbits[k] <= m
+            int lo = 0, hi = n_bins - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tbits[mid] <= m)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            bin = lo;
+        }
+        const int sgn = (Coef<T>::to_slot(v) >> (sizeof(T) * 8 - 1)) & 1;
+        atomicAdd(&hist_s[sgn * (n_bins + 1) + bin], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb2; k += blockDim.x)
+        if (hist_s[k]) atomicAdd(&counts[k], (unsigned long long)hist_s[k]);
+}
+
 // Start of an X layer inside a captured program: clears the layer counters
 // (not the error bits or the committed operator) and the per-qubit
 // population deltas, and records |O| entering the layer.

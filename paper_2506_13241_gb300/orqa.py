@@ -29,7 +29,8 @@ EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_se
             "orqa_last_error", "orqa_destroy", "orqa_expect_noalloc",
             "orqa_workspace_bytes_batch", "orqa_set_operator_batch", "orqa_apply_layer_batch",
             "orqa_expect_batch", "orqa_problem_sizes", "orqa_export_batch",
-            "orqa_run_program", "orqa_get_tuning", "orqa_set_tuning", "orqa_autotune"]
+            "orqa_run_program", "orqa_get_tuning", "orqa_set_tuning", "orqa_autotune",
+            "orqa_apply_pauli_rotation", "orqa_histogram"]
 ORQA_NOALLOC_MAX_STRINGS = 1 << 27
 ORQA_MAX_PROBLEMS = 4096
 
@@ -142,6 +143,10 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_set_tuning.argtypes = [vp, tp]
         lib.orqa_autotune.restype = i32
         lib.orqa_autotune.argtypes = [vp, ldp, i32, i32, dp, i32, tp, dpp]
+        lib.orqa_apply_pauli_rotation.restype = i32
+        lib.orqa_apply_pauli_rotation.argtypes = [vp, vp, vp, dp, dp, i64p]
+        lib.orqa_histogram.restype = i32
+        lib.orqa_histogram.argtypes = [vp, i32, dp, i64p, dpp]
         _lib = lib
     return _lib
 
@@ -327,6 +332,26 @@ def orqa_apply_layer(ctx, gates, delta: float) -> int:
     return n.value
 
 
+def orqa_apply_pauli_rotation(ctx, xj: np.ndarray, zj: np.ndarray, theta: float, delta: float) -> int:
+    """One rotation exp(-i theta/2 sigma_J); xj, zj: the W plane words of J."""
+    xj = np.ascontiguousarray(xj, dtype=np.uint64).reshape(-1)
+    zj = np.ascontiguousarray(zj, dtype=np.uint64).reshape(-1)
+    n = ctypes.c_int64()
+    _check(ctx, library().orqa_apply_pauli_rotation(ctx, xj.ctypes.data, zj.ctypes.data, float(theta), float(delta),
+                                                    ctypes.byref(n)))
+    return n.value
+
+
+def orqa_histogram(ctx, n_bins: int, log10_lo: float):
+    """(counts [2, n_bins + 1] (row 0: c > 0, row 1: c < 0; column n_bins:
+    below the lowest edge), max|c|)."""
+    counts = np.zeros(2 * (n_bins + 1), dtype=np.int64)
+    mx = ctypes.c_double()
+    _check(ctx, library().orqa_histogram(ctx, n_bins, float(log10_lo),
+                                         counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(mx)))
+    return counts.reshape(2, n_bins + 1), mx.value
+
+
 def orqa_merge_truncate(ctx, delta: float) -> int:
     n = ctypes.c_int64()
     _check(ctx, library().orqa_merge_truncate(ctx, float(delta), ctypes.byref(n)))
@@ -490,6 +515,14 @@ class Context:
 
     def merge_truncate(self, delta: float = 0.0) -> int:
         return orqa_merge_truncate(self.ctx, delta)
+
+    def histogram(self, n_bins: int, log10_lo: float):
+        return orqa_histogram(self.ctx, n_bins, log10_lo)
+
+    def apply_pauli_rotation(self, label: str, theta: float, delta: float = 0.0) -> int:
+        """Rotation about the Pauli string `label` (character q = qubit q)."""
+        x, z = strings_from_labels([label], self.n_qubits)
+        return orqa_apply_pauli_rotation(self.ctx, x[0], z[0], theta, delta)
 
     def expect(self) -> float:
         return orqa_expect(self.ctx)

@@ -342,3 +342,25 @@ def test_planted_mistakes_are_caught(oracle_mod, tmp_path, mutation):
     if len(op) != 1:
         caught.append("clifford")
     assert caught, "mutation %d escaped every pin" % mutation
+
+
+def test_histogram_hand_example(oracle_mod):
+    """D_t(x) counts on a hand-checked example: n_bins = 2 over
+    log10|x| in [-4, 0] gives edges 1e-4 and 1e-2 times max|c| = 1."""
+    counts, m = oracle_mod.histogram([1.0, -0.5, 0.01, -1e-7, 0.3, 2e-3, -5e-5], 2, -4.0)
+    assert m == 1.0
+    assert counts.tolist() == [[0 + 1, 3, 0], [0, 1, 2]]
+
+
+def test_histogram_invariants(oracle_mod):
+    """Every string lands in exactly one bin; the largest is in the top
+    bin; scaling all coefficients by a power of two changes nothing."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal(5000) * 10.0 ** rng.uniform(-8, 0, 5000)
+    counts, m = oracle_mod.histogram(c, 16, -8.0)
+    assert counts.sum() == c.size
+    top = 0 if c[np.argmax(np.abs(c))] > 0 else 1
+    assert counts[top, 15] >= 1
+    scaled, m2 = oracle_mod.histogram(c * 0.25, 16, -8.0)
+    assert m2 == m * 0.25 and (scaled == counts).all()
