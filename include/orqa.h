@@ -78,11 +78,13 @@ enum {
                                 |c| <= eps0 * max|c|, the max taken over the
                                 operator after each gate's updates */
     ORQA_FLAG_FP32 = 4       /* precision form: coefficients stored and
-                                multiplied in FP32; two-member pair updates
-                                (the merges of Algorithm 1) evaluated with the
-                                compensated Dot2 scheme; duplicate merging of
-                                input and <0|O|0> accumulate in FP64.  The ABI
-                                still takes and returns FP64 arrays. */
+                                multiplied in FP32, with cos and sin carried
+                                as float pairs hi + lo; two-member pair
+                                updates (the merges of Algorithm 1) evaluated
+                                with the compensated Dot2 scheme; duplicate
+                                merging of input and <0|O|0> accumulate in
+                                FP64.  The ABI still takes and returns FP64
+                                arrays. */
 };
 
 /* Most problems one batched context may hold. */
