@@ -67,7 +67,7 @@ struct orqa_ctx {
     int sub_max = LB_MAX;          // most strings of one shared-memory sub-range
     int bucket_density = 16;       // strings per fine bucket at full capacity
     int n_fine_max = 0;            // fine-bucket arrays are sized for this many
-    int grid_per_sm = 8;           // CTAs per SM of the streaming kernels
+    int grid_per_sm = 16;          // CTAs per SM of the streaming kernels
     // captured programs (one per starting buffer) and their device results
     cudaStream_t cap_stream = nullptr;
     cudaStream_t body_stream = nullptr;
@@ -667,7 +667,7 @@ RxLists rx_lists(orqa_ctx* ctx, int S) {
 
 int local_grid(const orqa_ctx* ctx, long long n_active) {
     const long long ranges = (n_active + ctx->range_target - 1) / ctx->range_target;
-    const long long cap = (long long)ctx->sm_count * 3;  // resident CTAs of the unit kernel
+    const long long cap = (long long)ctx->sm_count * LB_CTAS_PER_SM;  // resident CTAs of the unit kernel
     return (int)std::max(1ll, std::min(ranges, cap));
 }
 
@@ -1460,7 +1460,7 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
     int cur = ctx->cur;
     size_t off = 0;
     const int g_stream = ctx->sm_count * ctx->grid_per_sm;
-    const int g_local = ctx->sm_count * 3;
+    const int g_local = ctx->sm_count * LB_CTAS_PER_SM;
     cudaGraph_t graph = nullptr;
     ctx->profile = false;
     ctx->stream = cs;

@@ -16,9 +16,11 @@
 //   1. fine-bucket counts of the active strings (filled by the kernel that
 //      wrote them): bucket = top bits of the hash of the unit key;
 //   2. exclusive scan of the counts;
-//   3. one streaming scatter of the active strings into bucket order;
-//   4. one CTA per contiguous range of ~LB_TARGET strings (whole buckets, so
-//      whole units) builds the units in shared memory and updates them there.
+//   3. one streaming scatter of the active strings into bucket order (which
+//      also clears the counts for the next pass);
+//   4. persistent CTAs claim contiguous ranges of ~range_target strings
+//      (whole buckets, so whole units), build the units in shared memory and
+//      update them there.
 // Survivors are appended to the output list (no chunk left) or to the next
 // active list, whose bucket counts are accumulated on the fly.
 #pragma once
@@ -28,13 +30,14 @@
 namespace orqa {
 
 constexpr int LB_THREADS = 256;
+constexpr int LB_CTAS_PER_SM = 3;  // resident unit-kernel CTAs per SM (launch bound)
 constexpr int LB_WARPS = LB_THREADS / 32;
 constexpr int LB_MAX = 512;         // most strings one CTA sub-range may hold
-constexpr int LB_TARGET = 320;      // strings per CTA range, on average
+constexpr int LB_TARGET = 448;      // strings per CTA range, on average (default tuning)
 constexpr int LB_TABLE = 1024;      // shared-memory hash slots
 constexpr int LB_UPW = 16;          // units a warp owns per round (lanes 0..15)
 constexpr int LB_UPW_LOG = 4;
-constexpr int LB_RU = LB_WARPS * LB_UPW;  // units per round
+constexpr int LB_RU = LB_WARPS * LB_UPW;  // dense unit rows (LB_UPW per warp)
 constexpr int LB_LIST = LB_UPW * 16;      // most pairs of one level in a warp
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 8;
@@ -49,93 +52,8 @@ __device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int
 // run's first gate unless that gate acts on it first.  Active strings are
 // counted into their pass-0 fine bucket.
 // ---------------------------------------------------------------------------
-template <int W, typename T>
-__global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, StrList active, long long cap,
-                                                  const __grid_constant__ RxRun run, Counters* ctr,
-                                                  int32_t* fcount, int fshift) {
-    if (block_aborted(ctr)) return;
-    const long long n = min((long long)ctr->n_live, cap);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long n_round = (n + 31) & ~31ll;
-    const unsigned long long dbits = Coef<T>::threshold(run);
-    const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        uint64_t x[W], z[W];
-        T c = 0;
-        const bool live = i < n;
-        bool act = false, keep = false;
-        if (live) {
-            load_plane<W>(src.z, i, z);
-            c = sc[i];
-            uint64_t acc = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc |= z[w] & run.mask[w];
-            act = acc != 0;
-            keep = keep_t<T>(c, dbits);
-            if (act && !keep) {
-                uint64_t f[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
-                if (!bit_of<W>(f, run.q_first)) act = false;  // dropped before its gates
-            }
-        }
-        const bool to_done = live && !act && keep;
-        const long long sd = warp_append(to_done, &ctr->n_done);
-        const long long sa = warp_append(act, &ctr->n_next);
-        if (to_done || act) {
-            const long long slot = to_done ? sd : sa;
-            StrList dst = to_done ? done : active;
-            const unsigned pid = src.pid ? src.pid[i] : 0u;
-            load_plane<W>(src.x, i, x);
-            if (slot < cap) {
-                store_plane<W>(dst.x, slot, x);
-                store_plane<W>(dst.z, slot, z);
-                reinterpret_cast<T*>(dst.c)[slot] = c;
-                if (dst.pid) dst.pid[slot] = (uint16_t)pid;
-            } else {
-                atomicOr(&ctr->err, ERR_OVERFLOW);
-            }
-            if (act) {
-                int pos[CHUNK_BITS], np, idx;
-                bool more;
-                const uint64_t h = unit_key_hash<W>(x, z, run.mask, 0, pos, np, idx, more, pid);
-                const int rk = atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
-                if (slot < cap) {
-                    active.h[slot] = h;
-                    active.rank[slot] = rk;
-                }
-            }
-        }
-        const unsigned nd = __popc(__ballot_sync(FULL_MASK, live && !act && !keep));
-        if ((threadIdx.x & 31) == 0 && nd) {
-            atomicAdd(&ctr->dropped, (unsigned long long)nd);
-            atomicAdd(&ctr->split_dropped, (unsigned long long)nd);
-        }
-    }
-}
-
-// Pass bookkeeping between the kernels of an X layer (one thread): the list
-// just written becomes the active list of the next pass.  With use_cond it
-// also sets the condition of the enclosing graph loop (another pass is
-// needed iff strings are active and no error was raised).
-__global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHandle cond, int use_cond) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const unsigned long long na = ctr->n_next;
-    ctr->n_active = na;
-    ctr->n_next = 0;
-    ctr->range_cursor = 0;
-    ctr->pass = first ? 0 : ctr->pass + 1;
-    if (na > 0 && ctr->pass >= MAX_PASSES) atomicOr(&ctr->err, ERR_PASS_LIMIT);  // bounds the loop
-    const unsigned long long pk = ctr->n_done + na;
-    if (pk > ctr->peak) ctr->peak = pk;
-    if (use_cond) cudaGraphSetConditional(cond, (na > 0 && ctr->err == 0) ? 1u : 0u);
-}
-
-// ---------------------------------------------------------------------------
-// Exclusive scan of the fine-bucket counts (n = number of buckets, a
-// multiple of SCAN_TILE): tile sums, a one-block scan of the tile sums,
-// then offsets[b]; offsets[n] = total.
-// ---------------------------------------------------------------------------
+// Exclusive block-wide scan of one int per thread (all threads call it);
+// total receives the sum.
 __device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& total) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     int incl = v;
@@ -164,6 +82,129 @@ __device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& t
     __syncthreads();
     return r;
 }
+
+// Each block takes tiles of SPLIT_ITEMS strings per thread: all loads of a
+// tile are issued before any decision, and the tile's outputs are reserved
+// with one atomic per list (a block scan gives every string its slot).
+constexpr int SPLIT_ITEMS = 4;
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, StrList active, long long cap,
+                                                  const __grid_constant__ RxRun run, Counters* ctr,
+                                                  int32_t* fcount, int fshift) {
+    __shared__ int warp_tot[33];
+    __shared__ unsigned long long s_base[2];
+    if (block_aborted(ctr)) return;
+    const long long n = min((long long)ctr->n_live, cap);
+    const long long tile = (long long)blockDim.x * SPLIT_ITEMS;
+    const unsigned long long dbits = Coef<T>::threshold(run);
+    const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
+    unsigned my_drop = 0;
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < n; t0 += (long long)gridDim.x * tile) {  // block-uniform
+        uint64_t z[SPLIT_ITEMS][W];
+        T c[SPLIT_ITEMS];
+        int kind[SPLIT_ITEMS];  // 0: not live or dropped, 1: output list, 2: active list
+#pragma unroll
+        for (int k = 0; k < SPLIT_ITEMS; ++k) {
+            const long long i = t0 + (long long)k * blockDim.x + threadIdx.x;
+            kind[k] = 0;
+            c[k] = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) z[k][w] = 0;
+            if (i < n) {
+                load_plane<W>(src.z, i, z[k]);
+                c[k] = sc[i];
+            }
+        }
+        int nd = 0, na = 0;
+#pragma unroll
+        for (int k = 0; k < SPLIT_ITEMS; ++k) {
+            const long long i = t0 + (long long)k * blockDim.x + threadIdx.x;
+            if (i >= n) continue;
+            uint64_t f[W], acc = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                f[w] = z[k][w] & run.mask[w];
+                acc |= f[w];
+            }
+            const bool keep = keep_t<T>(c[k], dbits);
+            bool act = acc != 0;
+            if (act && !keep && !bit_of<W>(f, run.q_first)) act = false;  // dropped before its gates
+            kind[k] = act ? 2 : (keep ? 1 : 0);
+            nd += kind[k] == 1;
+            na += kind[k] == 2;
+            my_drop += kind[k] == 0;
+        }
+        int total;
+        const int pre = block_scan_exclusive(nd | (na << 16), warp_tot, total);
+        if (threadIdx.x == 0) {
+            const unsigned td = (unsigned)total & 0xffffu, ta = (unsigned)total >> 16;
+            s_base[0] = td ? atomicAdd(&ctr->n_done, (unsigned long long)td) : 0ull;
+            s_base[1] = ta ? atomicAdd(&ctr->n_next, (unsigned long long)ta) : 0ull;
+        }
+        __syncthreads();
+        long long sd = (long long)(s_base[0] + (unsigned)(pre & 0xffff));
+        long long sa = (long long)(s_base[1] + (unsigned)(pre >> 16));
+#pragma unroll
+        for (int k = 0; k < SPLIT_ITEMS; ++k) {
+            if (!kind[k]) continue;
+            const long long i = t0 + (long long)k * blockDim.x + threadIdx.x;
+            const bool act = kind[k] == 2;
+            const long long slot = act ? sa++ : sd++;
+            StrList dst = act ? active : done;
+            const unsigned pid = src.pid ? src.pid[i] : 0u;
+            uint64_t x[W];
+            load_plane<W>(src.x, i, x);
+            if (slot < cap) {
+                store_plane<W>(dst.x, slot, x);
+                store_plane<W>(dst.z, slot, z[k]);
+                reinterpret_cast<T*>(dst.c)[slot] = c[k];
+                if (dst.pid) dst.pid[slot] = (uint16_t)pid;
+            } else {
+                atomicOr(&ctr->err, ERR_OVERFLOW);
+            }
+            if (act) {
+                int pos[CHUNK_BITS], np, idx;
+                bool more;
+                const uint64_t h = unit_key_hash<W>(x, z[k], run.mask, 0, pos, np, idx, more, pid);
+                const int rk = atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
+                if (slot < cap) {
+                    active.h[slot] = h;
+                    active.rank[slot] = rk;
+                }
+            }
+        }
+        __syncthreads();  // s_base is rewritten by the next tile
+    }
+    const unsigned wd = __reduce_add_sync(FULL_MASK, my_drop);
+    if ((threadIdx.x & 31) == 0 && wd) {
+        atomicAdd(&ctr->dropped, (unsigned long long)wd);
+        atomicAdd(&ctr->split_dropped, (unsigned long long)wd);
+    }
+}
+
+// Pass bookkeeping between the kernels of an X layer (one thread): the list
+// just written becomes the active list of the next pass.  With use_cond it
+// also sets the condition of the enclosing graph loop (another pass is
+// needed iff strings are active and no error was raised).
+__global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHandle cond, int use_cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long na = ctr->n_next;
+    ctr->n_active = na;
+    ctr->n_next = 0;
+    ctr->range_cursor = 0;
+    ctr->pass = first ? 0 : ctr->pass + 1;
+    if (na > 0 && ctr->pass >= MAX_PASSES) atomicOr(&ctr->err, ERR_PASS_LIMIT);  // bounds the loop
+    const unsigned long long pk = ctr->n_done + na;
+    if (pk > ctr->peak) ctr->peak = pk;
+    if (use_cond) cudaGraphSetConditional(cond, (na > 0 && ctr->err == 0) ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the fine-bucket counts (n = number of buckets, a
+// multiple of SCAN_TILE): tile sums, a one-block scan of the tile sums,
+// then offsets[b]; offsets[n] = total.
+// ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int32_t* counts, long long* offsets,
                                                              long long* tile_sums, const Counters* ctr) {
@@ -343,33 +384,35 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
 // CTA-local unit processing.
 //
 // A CTA loads its range (whole fine buckets, so whole units) into shared
-// memory and groups the strings into units with a shared-memory hash table on
-// the exact key (z, x outside the chunk).  Units are processed LB_RU per
-// round: a unit is a 32-slot row (slot = the string's chunk bits) with a
-// 32-bit occupancy mask.  For chunk level j the pair {slot l, slot l | 2^j}
-// (bit j of l clear) holds the strings P (sigma_z at the level's qubit q) and
+// memory, groups the strings into units with a shared-memory hash table on
+// the exact key (z, x outside the chunk) and lists the strings of every unit
+// contiguously.  A unit is a 32-slot row (slot = the string's chunk bits)
+// with a 32-bit occupancy mask.  Each warp claims groups of LB_UPW units
+// from a shared cursor and processes them with warp-level synchronisation
+// only.  For chunk level j the pair {slot l, slot l | 2^j} (bit j of l
+// clear) holds the strings P (sigma_z at the level's qubit q) and
 // P xor X_q (sigma_y); by Eq. (update_rule) with B(Z,X) = 1, B(Y,X) = -1,
 //     new c_Z = cos c_Z - sin c_Y,   new c_Y = cos c_Y + sin c_Z,
 // an absent member counting as 0 (Algorithm 1 inserts it), then the
-// truncation c == 0 or |c| < delta.  Every stage is flattened over the block:
-// the pairs of a level (found with two mask operations per unit) go to
-// block-wide lists -- one member present: 2 DMUL, both: 4 DMUL + 2 DADD --
-// processed by all threads, and the outputs of a round are enumerated one
-// per thread.  FP64 instructions thus run on full warps (GB300 issues FP64
-// at 2 lanes per clock per SM whatever the active mask) and no thread loops
-// over one unit's members.
+// truncation c == 0 or |c| < delta.  The pairs of a level (found with two
+// mask operations per unit) go to warp lists -- one member present: 2 DMUL,
+// both: 4 DMUL + 2 DADD -- processed by all lanes, and the outputs of a
+// group are enumerated one per lane.  FP64 instructions thus run on full
+// warps (GB300 issues FP64 at 2 lanes per clock per SM whatever the active
+// mask) and no lane loops over one unit's members.
 // ---------------------------------------------------------------------------
 template <int W, typename T>
 struct LocalSmem {
     uint64_t sx[W][LB_MAX];     // x with the chunk bits cleared
     uint64_t sz[W][LB_MAX];
     T sc[LB_MAX];
-    T dense[LB_RU][32];
+    T dense[LB_RU][33];         // unit rows, padded so equal slots of different rows use different banks
     int32_t table[LB_TABLE];
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
-    int16_t rep_uid[LB_MAX];
+    int16_t rep_uid[LB_MAX];    // unit id of a representative, then the strings in unit order
     int16_t u_rep[LB_MAX];
+    int16_t ustart[LB_MAX + 1]; // first position of each unit in that order
     uint16_t spid[LB_MAX];      // problem index of each string
     uint16_t list1[LB_WARPS][LB_LIST];
     uint16_t list2[LB_WARPS][LB_LIST];
@@ -377,8 +420,7 @@ struct LocalSmem {
     uint8_t s_idx[LB_MAX];
     int blk_delta[MAX_QUBITS];
     int warp_tot[33];
-    unsigned warp_cnt[LB_WARPS];
-    unsigned long long warp_base[2][LB_WARPS];
+    int group_cursor;           // next unit group a warp claims
     long long range[2];
     int bucket_range[3];
     int n_units;
@@ -430,7 +472,7 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 // sub_max <= LB_MAX strings (the load of the shared-memory hash table is at
 // most sub_max / LB_TABLE).
 template <int W, typename T>
-__global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
+__global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const void* bk, const long long* __restrict__ offsets, const int32_t* __restrict__ range_start,
     long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
     StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift, unsigned long long* pop_delta) {
@@ -560,14 +602,56 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
         if (tid == 0) S.n_units = total;
     }
     __syncthreads();
-    for (int i = tid; i < m; i += LB_THREADS) S.s_unit[i] = S.rep_uid[S.s_unit[i]];
-    __syncthreads();
     const int n_units = S.n_units;
+    // ---- the strings of each unit as a contiguous list (counts in the hash
+    // table, which is free now; the order list reuses rep_uid once read)
+    for (int u = tid; u < n_units; u += LB_THREADS) S.table[u] = 0;
+    __syncthreads();
+    for (int i = tid; i < m; i += LB_THREADS) {
+        const int u = S.rep_uid[S.s_unit[i]];
+        S.s_unit[i] = (int16_t)u;
+        atomicAdd(&S.table[u], 1);
+    }
+    __syncthreads();
+    {
+        int v[PER_T], cnt = 0;
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k) {
+            const int u = tid * PER_T + k;
+            v[k] = u < n_units ? S.table[u] : 0;
+            cnt += v[k];
+        }
+        int total;
+        int run = block_scan_exclusive(cnt, S.warp_tot, total);
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k) {
+            const int u = tid * PER_T + k;
+            if (u < n_units) S.ustart[u] = (int16_t)run;
+            run += v[k];
+        }
+        if (tid == 0) {
+            S.ustart[n_units] = (int16_t)total;
+            S.group_cursor = 0;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += LB_THREADS) {
+        const int u = S.s_unit[i];
+        const int k = atomicSub(&S.table[u], 1) - 1;
+        S.rep_uid[S.ustart[u] + k] = (int16_t)i;
+    }
+    __syncthreads();
 
-    // ---- rounds: warp wp owns units rbase + wp*LB_UPW + lane for lanes < LB_UPW
-    const int ub = wp * LB_UPW;  // first unit row of this warp
-    for (int rbase = 0; rbase < n_units; rbase += LB_RU) {
-        const int u = rbase + ub + lane;
+    // ---- unit groups: a warp claims LB_UPW consecutive units at a time
+    // (lane L < LB_UPW owns unit g + L, in dense row ub + L) and works on
+    // them with warp-level synchronisation only
+    const int ub = wp * LB_UPW;  // first dense row of this warp
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(&S.group_cursor, LB_UPW);
+        g = __shfl_sync(FULL_MASK, g, 0);
+        if (g >= n_units) break;  // warp-uniform
+        const int u = g + lane;
         const bool own = lane < LB_UPW && u < n_units;
         uint64_t z[W], xb[W], xn[W];
         int pos[CHUNK_BITS] = {0, 0, 0, 0, 0}, pos2[CHUNK_BITS] = {0, 0, 0, 0, 0};
@@ -596,10 +680,13 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
         }
         if (lane < LB_UPW) S.occ[ub + lane] = 0u;
         __syncwarp();
-        // strings of this warp's units into their slots
-        for (int i = lane; i < m; i += 32) {
-            const int ul = S.s_unit[i] - (rbase + ub);
-            if (ul >= 0 && ul < LB_UPW) {
+        // strings of this warp's units into their slots (a contiguous run of
+        // the unit-ordered list)
+        {
+            const int k_lo = S.ustart[g], k_hi = S.ustart[min(g + LB_UPW, n_units)];
+            for (int k = k_lo + lane; k < k_hi; k += 32) {
+                const int i = S.rep_uid[k];
+                const int ul = S.s_unit[i] - g;
                 const int l = S.s_idx[i];
                 S.dense[ub + ul][l] = S.sc[i];
                 atomicOr(&S.occ[ub + ul], 1u << l);
@@ -672,28 +759,19 @@ __global__ void __launch_bounds__(LB_THREADS, 3) k_bucket_local(
                 if (d) atomicAdd(&S.blk_delta[pos[j]], d);
             }
         }
-        // ---- outputs: flattened over the warp, one reservation per block
+        // ---- outputs: flattened over the warp, one reservation per warp and list
         const unsigned occ = own ? S.occ[ub + lane] : 0u;
         const unsigned nout = __popc(occ);
         unsigned wtot;
         const unsigned flat = warp_exclusive_scan(nout, wtot);
         unsigned ntot;
         const unsigned noff = warp_exclusive_scan(more ? nout : 0u, ntot);
-        if (lane == 0) S.warp_cnt[wp] = (wtot - ntot) | (ntot << 16);
-        __syncthreads();
-        if (tid < 2) {
-            unsigned long long tot = 0;
-            for (int k = 0; k < LB_WARPS; ++k) {
-                S.warp_base[tid][k] = tot;
-                const unsigned wc = S.warp_cnt[k];
-                tot += (tid == 0) ? (wc & 0xffffu) : (wc >> 16);
-            }
-            unsigned long long b = 0;
-            if (tot) b = atomicAdd(tid == 0 ? &ctr->n_done : &ctr->n_next, tot);
-            for (int k = 0; k < LB_WARPS; ++k) S.warp_base[tid][k] += b;
+        unsigned long long bd = 0, bn = 0;
+        if (lane == 0) {
+            if (wtot > ntot) bd = atomicAdd(&ctr->n_done, (unsigned long long)(wtot - ntot));
+            if (ntot) bn = atomicAdd(&ctr->n_next, (unsigned long long)ntot);
         }
-        __syncthreads();
-        const unsigned long long base_done = S.warp_base[0][wp], base_next = S.warp_base[1][wp];
+        const unsigned long long base_done = shfl64(bd, 0), base_next = shfl64(bn, 0);
         const unsigned doff = flat - noff;  // done-list offset of this lane's unit
         for (unsigned kb = 0; kb < wtot; kb += 32) {
             const unsigned k = kb + lane;
