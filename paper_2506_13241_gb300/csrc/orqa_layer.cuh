@@ -406,13 +406,15 @@ struct LocalSmem {
     uint64_t sx[W][LB_MAX];     // x with the chunk bits cleared
     uint64_t sz[W][LB_MAX];
     T sc[LB_MAX];
-    T dense[LB_RU][33];         // unit rows, padded so equal slots of different rows use different banks
+    T dense[LB_RU][32];         // unit rows (slot = chunk bits)
     int32_t table[LB_TABLE];
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
-    int16_t rep_uid[LB_MAX];    // unit id of a representative, then the strings in unit order
+    int16_t rep_uid[LB_MAX];    // unit id of a representative
     int16_t u_rep[LB_MAX];
+    int16_t s_order[LB_MAX];    // the strings in unit order
     int16_t ustart[LB_MAX + 1]; // first position of each unit in that order
+    int32_t rep_cnt[LB_MAX / 2]; // strings per representative, two 16-bit counts per word
     uint16_t spid[LB_MAX];      // problem index of each string
     uint16_t list1[LB_WARPS][LB_LIST];
     uint16_t list2[LB_WARPS][LB_LIST];
@@ -515,6 +517,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         S.bucket_range[2] = lo;
     }
     for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = -1;
+    for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.rep_cnt[t] = 0;
+    if (tid == 0) S.n_units = 0;
     __syncthreads();
     const long long s0 = S.range[0];
     const int m = (int)(S.range[1] - S.range[0]);
@@ -576,49 +580,27 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             slot = (slot + 1) & (LB_TABLE - 1);
         }
         S.s_unit[i] = (int16_t)rep;
-    }
-    __syncthreads();
-    // ---- number the units (representatives in string order)
-    constexpr int PER_T = LB_MAX / LB_THREADS;
-    {
-        int flags[PER_T], cnt = 0;
-#pragma unroll
-        for (int k = 0; k < PER_T; ++k) {
-            const int i = tid * PER_T + k;
-            flags[k] = (i < m && S.s_unit[i] == i) ? 1 : 0;
-            cnt += flags[k];
+        if (rep == i) {  // a new unit: its id, in arbitrary order
+            const int u = atomicAdd(&S.n_units, 1);
+            S.rep_uid[i] = (int16_t)u;
+            S.u_rep[u] = (int16_t)i;
         }
-        int total;
-        int id = block_scan_exclusive(cnt, S.warp_tot, total);
-#pragma unroll
-        for (int k = 0; k < PER_T; ++k) {
-            const int i = tid * PER_T + k;
-            if (flags[k]) {
-                S.rep_uid[i] = (int16_t)id;
-                S.u_rep[id] = (int16_t)i;
-                ++id;
-            }
-        }
-        if (tid == 0) S.n_units = total;
+        atomicAdd(&S.rep_cnt[rep >> 1], 1 << (16 * (rep & 1)));
     }
     __syncthreads();
     const int n_units = S.n_units;
-    // ---- the strings of each unit as a contiguous list (counts in the hash
-    // table, which is free now; the order list reuses rep_uid once read)
-    for (int u = tid; u < n_units; u += LB_THREADS) S.table[u] = 0;
-    __syncthreads();
-    for (int i = tid; i < m; i += LB_THREADS) {
-        const int u = S.rep_uid[S.s_unit[i]];
-        S.s_unit[i] = (int16_t)u;
-        atomicAdd(&S.table[u], 1);
-    }
-    __syncthreads();
+    // ---- the strings of each unit as a contiguous list
+    constexpr int PER_T = LB_MAX / LB_THREADS;
     {
         int v[PER_T], cnt = 0;
 #pragma unroll
         for (int k = 0; k < PER_T; ++k) {
             const int u = tid * PER_T + k;
-            v[k] = u < n_units ? S.table[u] : 0;
+            v[k] = 0;
+            if (u < n_units) {
+                const int r = S.u_rep[u];
+                v[k] = (S.rep_cnt[r >> 1] >> (16 * (r & 1))) & 0xffff;
+            }
             cnt += v[k];
         }
         int total;
@@ -636,9 +618,11 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     }
     __syncthreads();
     for (int i = tid; i < m; i += LB_THREADS) {
-        const int u = S.s_unit[i];
-        const int k = atomicSub(&S.table[u], 1) - 1;
-        S.rep_uid[S.ustart[u] + k] = (int16_t)i;
+        const int r = S.s_unit[i];
+        const int u = S.rep_uid[r];
+        const int k = ((atomicSub(&S.rep_cnt[r >> 1], 1 << (16 * (r & 1))) >> (16 * (r & 1))) & 0xffff) - 1;
+        S.s_order[S.ustart[u] + k] = (int16_t)i;
+        S.s_unit[i] = (int16_t)u;
     }
     __syncthreads();
 
@@ -685,7 +669,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         {
             const int k_lo = S.ustart[g], k_hi = S.ustart[min(g + LB_UPW, n_units)];
             for (int k = k_lo + lane; k < k_hi; k += 32) {
-                const int i = S.rep_uid[k];
+                const int i = S.s_order[k];
                 const int ul = S.s_unit[i] - g;
                 const int l = S.s_idx[i];
                 S.dense[ub + ul][l] = S.sc[i];
