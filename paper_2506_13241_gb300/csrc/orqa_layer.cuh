@@ -501,20 +501,33 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const int b_end = S.bucket_range[1];
     for (int b_lo = S.bucket_range[0]; b_lo < b_end;) {  // block-uniform
     __syncthreads();  // everyone has read the previous sub-range's bounds
-    if (tid == 0) {
-        // last bucket boundary b <= b_end with offsets[b] - offsets[b_lo] <= sub_max
+    if (wp == 0) {
+        // last bucket boundary b <= b_end with offsets[b] - offsets[b_lo] <=
+        // sub_max, by a 32-way search: the offsets are nondecreasing, so of
+        // 32 boundaries spread over [lo, hi] the qualifying ones form a
+        // prefix, and each step shrinks the interval 32-fold (a range can
+        // span many empty buckets when few strings are active)
         const long long base = offsets[b_lo];
-        int lo = b_lo, hi = b_end;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] - base <= sub_max)
-                lo = mid;
-            else
-                hi = mid - 1;
+        int lo = b_lo, hi = b_end;  // lo qualifies; the answer lies in [lo, hi]
+        while (lo < hi) {           // warp-uniform
+            const long long span = hi - lo;
+            const int cand = lo + (int)((span * (lane + 1) + 31) >> 5);  // nondecreasing, last = hi
+            const unsigned bal = __ballot_sync(FULL_MASK, offsets[cand] - base <= sub_max);
+            const int K = __popc(bal);
+            if (K == 32) {
+                lo = hi;
+                break;
+            }
+            const int first_bad = __shfl_sync(FULL_MASK, cand, K);
+            const int last_good = __shfl_sync(FULL_MASK, cand, K > 0 ? K - 1 : 0);
+            if (K > 0) lo = last_good;
+            hi = first_bad - 1;
         }
-        S.range[0] = base;
-        S.range[1] = offsets[lo];
-        S.bucket_range[2] = lo;
+        if (lane == 0) {
+            S.range[0] = base;
+            S.range[1] = offsets[lo];
+            S.bucket_range[2] = lo;
+        }
     }
     for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = -1;
     for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.rep_cnt[t] = 0;
