@@ -334,21 +334,34 @@ __device__ __forceinline__ void load_record(const void* base, long long i, uint6
     }
 }
 
-constexpr int record_bytes(int W) { return W == 2 ? 64 : 32; }
+__host__ __device__ constexpr int record_bytes(int W) { return W == 2 ? 64 : 32; }
 
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const unsigned lo = __shfl_sync(FULL_MASK, (unsigned)v, src);
+    const unsigned hi = __shfl_sync(FULL_MASK, (unsigned)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// The records of 32 strings are staged in shared memory and written back
+// cooperatively: RQ = record_bytes / 16 consecutive lanes store the 16-byte
+// quarters of one record, so every store instruction writes 32 / RQ whole
+// records instead of 32 scattered 16-byte pieces.
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long cap, int fshift,
                                                         const long long* __restrict__ offsets, void* dst,
                                                         int32_t* fcount, long long n_fine, Counters* ctr) {
+    constexpr int RQ = record_bytes(W) / 16;  // 16-byte quarters per record
+    __shared__ uint4 stage[256 / 32][32][RQ];
     if (block_aborted(ctr)) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const long long n = min((long long)ctr->n_active, cap);
     // the counts were consumed by the scan; clear them for the next pass
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < n_fine;
          b += (long long)gridDim.x * blockDim.x)
         fcount[b] = 0;
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
-    for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x; base < n;
-         base += stride) {
+    for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x;
+         base - threadIdx.x < n; base += stride) {  // warp-uniform: all lanes iterate together
         long long slot[SCATTER_ILP];
         uint64_t h[SCATTER_ILP];
 #pragma unroll
@@ -367,15 +380,39 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
-            if (slot[k] < 0) continue;
-            if (slot[k] >= cap) {  // only reachable after an undetected count error; never write past the records
+            long long sl = slot[k];
+            if (sl >= cap) {  // only reachable after an undetected count error; never write past the records
                 atomicOr(&ctr->err, ERR_OVERFLOW);
-                continue;
+                sl = -1;
             }
-            uint64_t x[W], z[W];
-            load_plane<W>(src.x, i, x);
-            load_plane<W>(src.z, i, z);
-            store_record<W, T>(dst, slot[k], x, z, reinterpret_cast<const T*>(src.c)[i], h[k]);
+            if (sl >= 0) {
+                uint64_t x[W], z[W];
+                load_plane<W>(src.x, i, x);
+                load_plane<W>(src.z, i, z);
+                const T c = reinterpret_cast<const T*>(src.c)[i];
+                if constexpr (W == 2) {
+                    stage[wp][lane][0] = make_uint4((unsigned)x[0], (unsigned)(x[0] >> 32), (unsigned)x[1],
+                                                    (unsigned)(x[1] >> 32));
+                    stage[wp][lane][1] = make_uint4((unsigned)z[0], (unsigned)(z[0] >> 32), (unsigned)z[1],
+                                                    (unsigned)(z[1] >> 32));
+                } else {
+                    stage[wp][lane][0] = make_uint4((unsigned)x[0], (unsigned)(x[0] >> 32), (unsigned)z[0],
+                                                    (unsigned)(z[0] >> 32));
+                }
+                const unsigned long long cs = Coef<T>::to_slot(c);
+                stage[wp][lane][RQ == 4 ? 2 : 1] =
+                    make_uint4((unsigned)cs, (unsigned)(cs >> 32), (unsigned)h[k], (unsigned)(h[k] >> 32));
+                if constexpr (RQ == 4) stage[wp][lane][3] = make_uint4(0u, 0u, 0u, 0u);  // completes the sector
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < RQ; ++r) {
+                const int rec = r * (32 / RQ) + lane / RQ, qi = lane % RQ;
+                const long long s_rec = (long long)shfl64((uint64_t)sl, rec);
+                if (s_rec >= 0)
+                    reinterpret_cast<uint4*>(dst)[s_rec * RQ + qi] = stage[wp][rec][qi];
+            }
+            __syncwarp();
         }
     }
 }
@@ -461,11 +498,6 @@ __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, unsigned& to
     return incl - v;
 }
 
-__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
-    const unsigned lo = __shfl_sync(FULL_MASK, (unsigned)v, src);
-    const unsigned hi = __shfl_sync(FULL_MASK, (unsigned)(v >> 32), src);
-    return ((uint64_t)hi << 32) | lo;
-}
 
 // Persistent: each CTA claims ranges from a device cursor until none is
 // left, so the grid can be fixed (as in a captured graph) and uneven ranges
