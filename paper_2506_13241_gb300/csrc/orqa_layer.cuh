@@ -438,6 +438,13 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
 // warps (GB300 issues FP64 at 2 lanes per clock per SM whatever the active
 // mask) and no lane loops over one unit's members.
 // ---------------------------------------------------------------------------
+// One work item of the unit kernel: buckets [b_lo, b_next) of range rj
+// (whose buckets end at b_end), holding strings [s0, s1) of the bucket order.
+struct SubRange {
+    long long s0, s1;
+    int rj, b_lo, b_next, b_end;
+};
+
 template <int W, typename T>
 struct LocalSmem {
     uint64_t sx[W][LB_MAX];     // x with the chunk bits cleared
@@ -460,10 +467,8 @@ struct LocalSmem {
     int blk_delta[MAX_QUBITS];
     int warp_tot[33];
     int group_cursor;           // next unit group a warp claims
-    long long range[2];
-    int bucket_range[3];
+    SubRange cur, nx;           // the sub-range in work and the next one
     int n_units;
-    int claim;
 };
 
 __device__ __forceinline__ unsigned level_mask(int j) {
@@ -499,6 +504,66 @@ __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, unsigned& to
 }
 
 
+// Prepares the next work item (one warp, all lanes): the rest of the
+// current range, or else the next non-empty range claimed from the device
+// cursor.  Its end is the last bucket boundary b <= b_end with
+// offsets[b] - offsets[b_lo] <= sub_max, found by a 32-way search: the
+// offsets are nondecreasing, so of 32 boundaries spread over [lo, hi] the
+// qualifying ones form a prefix, and each step shrinks the interval 32-fold
+// (a range can span many empty buckets when few strings are active).
+template <typename Smem>
+__device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int32_t* __restrict__ range_start,
+                                              const long long* __restrict__ offsets, long long J, int sub_max,
+                                              bool first) {
+    const int lane = threadIdx.x & 31;
+    int rj, b_lo, b_end;
+    if (!first && S.cur.b_next < S.cur.b_end) {
+        rj = S.cur.rj;
+        b_lo = S.cur.b_next;
+        b_end = S.cur.b_end;
+    } else {
+        for (;;) {  // warp-uniform; skips empty ranges
+            int r = 0;
+            if (lane == 0) r = (int)atomicAdd(&ctr->range_cursor, 1u);
+            r = __shfl_sync(FULL_MASK, r, 0);
+            rj = r;
+            if (r >= J) break;
+            b_lo = range_start[r];
+            b_end = range_start[r + 1];
+            if (b_lo < b_end) break;
+        }
+    }
+    if (rj >= J) {
+        if (lane == 0) S.nx.rj = rj;
+        return;
+    }
+    const long long base = offsets[b_lo];
+    int lo = b_lo, hi = b_end;  // lo qualifies; the answer lies in [lo, hi]
+    while (lo < hi) {           // warp-uniform
+        const long long span = hi - lo;
+        const int cand = lo + (int)((span * (lane + 1) + 31) >> 5);  // nondecreasing, last = hi
+        const unsigned bal = __ballot_sync(FULL_MASK, offsets[cand] - base <= sub_max);
+        const int K = __popc(bal);
+        if (K == 32) {
+            lo = hi;
+            break;
+        }
+        const int first_bad = __shfl_sync(FULL_MASK, cand, K);
+        const int last_good = __shfl_sync(FULL_MASK, cand, K > 0 ? K - 1 : 0);
+        if (K > 0) lo = last_good;
+        hi = first_bad - 1;
+    }
+    const long long end = offsets[lo];
+    if (lane == 0) {
+        S.nx.rj = rj;
+        S.nx.b_lo = b_lo;
+        S.nx.b_next = lo;
+        S.nx.b_end = b_end;
+        S.nx.s0 = base;
+        S.nx.s1 = end;
+    }
+}
+
 // Persistent: each CTA claims ranges from a device cursor until none is
 // left, so the grid can be fixed (as in a captured graph) and uneven ranges
 // balance across CTAs.  The number of ranges J = ceil(total / range_target)
@@ -520,60 +585,27 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
 
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) S.blk_delta[t] = 0;
     unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
+    // The work items are sub-ranges; the next one (claiming a new range when
+    // the current range is done) is prepared by warp LB_WARPS - 1 while the
+    // other warps work on the current one's units, so the latency of the
+    // claim and the bound search overlaps useful work.
+    if (wp == LB_WARPS - 1) next_subrange(S, ctr, range_start, offsets, J, sub_max, true);
     for (;;) {  // block-uniform
-    if (tid == 0) S.claim = (int)atomicAdd(&ctr->range_cursor, 1u);
-    __syncthreads();
-    const int rj = S.claim;
-    if (rj >= J) break;
-    // ---- range rj: whole buckets whose start lies in [rj*T, (rj+1)*T)
-    // (found by the scan), processed in sub-ranges of whole buckets that fit
-    // in shared memory
-    if (tid < 2) S.bucket_range[tid] = range_start[rj + tid];
-    __syncthreads();
-    const int b_end = S.bucket_range[1];
-    for (int b_lo = S.bucket_range[0]; b_lo < b_end;) {  // block-uniform
-    __syncthreads();  // everyone has read the previous sub-range's bounds
-    if (wp == 0) {
-        // last bucket boundary b <= b_end with offsets[b] - offsets[b_lo] <=
-        // sub_max, by a 32-way search: the offsets are nondecreasing, so of
-        // 32 boundaries spread over [lo, hi] the qualifying ones form a
-        // prefix, and each step shrinks the interval 32-fold (a range can
-        // span many empty buckets when few strings are active)
-        const long long base = offsets[b_lo];
-        int lo = b_lo, hi = b_end;  // lo qualifies; the answer lies in [lo, hi]
-        while (lo < hi) {           // warp-uniform
-            const long long span = hi - lo;
-            const int cand = lo + (int)((span * (lane + 1) + 31) >> 5);  // nondecreasing, last = hi
-            const unsigned bal = __ballot_sync(FULL_MASK, offsets[cand] - base <= sub_max);
-            const int K = __popc(bal);
-            if (K == 32) {
-                lo = hi;
-                break;
-            }
-            const int first_bad = __shfl_sync(FULL_MASK, cand, K);
-            const int last_good = __shfl_sync(FULL_MASK, cand, K > 0 ? K - 1 : 0);
-            if (K > 0) lo = last_good;
-            hi = first_bad - 1;
-        }
-        if (lane == 0) {
-            S.range[0] = base;
-            S.range[1] = offsets[lo];
-            S.bucket_range[2] = lo;
-        }
+    __syncthreads();  // the prepared item is visible; the previous one is finished
+    if (tid == 0) {
+        S.cur = S.nx;
+        S.n_units = 0;
     }
     for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = -1;
     for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.rep_cnt[t] = 0;
-    if (tid == 0) S.n_units = 0;
     __syncthreads();
-    const long long s0 = S.range[0];
-    const int m = (int)(S.range[1] - S.range[0]);
-    const int b_next = S.bucket_range[2];
-    if (b_next == b_lo) {  // one bucket alone exceeds sub_max
+    if (S.cur.rj >= J) break;
+    if (S.cur.b_next == S.cur.b_lo) {  // one bucket alone exceeds sub_max
         if (tid == 0) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
         break;
     }
-    b_lo = b_next;
-    if (m == 0) continue;
+    const long long s0 = S.cur.s0;
+    const int m = (int)(S.cur.s1 - S.cur.s0);
 
     // ---- load the range; key of a string = (z, x with the chunk bits cleared)
     for (int i = tid; i < m; i += LB_THREADS) {
@@ -675,6 +707,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     // (lane L < LB_UPW owns unit g + L, in dense row ub + L) and works on
     // them with warp-level synchronisation only
     const int ub = wp * LB_UPW;  // first dense row of this warp
+    if (wp == LB_WARPS - 1) next_subrange(S, ctr, range_start, offsets, J, sub_max, false);
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(&S.group_cursor, LB_UPW);
@@ -869,8 +902,6 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             }
         }
         __syncwarp();
-    }
-    __syncthreads();  // shared arrays are reused by the next sub-range
     }
     }
     const unsigned nb = __reduce_add_sync(FULL_MASK, (unsigned)my_branch);
