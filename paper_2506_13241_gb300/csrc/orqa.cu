@@ -62,7 +62,7 @@ struct orqa_ctx {
     // X-layer passes (fine buckets)
     int n_fine = 0;
     int fshift = 0;
-    int32_t* fcount = nullptr;
+    uint32_t* fcount = nullptr;     // 16-bit counts, two per word
     int range_target = LB_TARGET;  // strings per unit-kernel range
     int sub_max = LB_MAX;          // most strings of one shared-memory sub-range
     int bucket_density = 16;       // strings per fine bucket at full capacity
@@ -204,7 +204,7 @@ Layout layout(int n_qubits, long long cap, int P) {
     size_t t = 0;
     t += 3 * (2 * L.str_x + L.str_c + L.str_pid);  // three string buffers
     t += L.shared;                         // layer / merge scratch
-    t += align_up(F * 4);                  // fine counts
+    t += align_up(F * 2);                  // fine counts (16 bits each)
     t += align_up((F + 1) * 8);            // fine offsets
     t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
     t += align_up(((size_t)(cap / MIN_RANGE_TARGET) + 2) * 4);  // unit-kernel range starts
@@ -704,7 +704,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     const long long n_in = ctx->n;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 4, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 2, ctx->stream));
     int r_split = -1;
     if (n_in > 0) {
         r_split = prof_begin(ctx, K_SPLIT, 0);
@@ -1091,7 +1091,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->n_fine_max = (int)L.n_fine;
     ctx->n_fine = (int)fine_buckets(cfg->capacity, ctx->bucket_density);
     ctx->fshift = 64 - __builtin_ctzll((unsigned long long)ctx->n_fine);
-    ctx->fcount = (int32_t*)p; p += align_up(F * 4);
+    ctx->fcount = (uint32_t*)p; p += align_up(F * 2);
     ctx->foffsets = (long long*)p; p += align_up((F + 1) * 8);
     ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
     ctx->range_start = (int32_t*)p; p += align_up(((size_t)(cfg->capacity / MIN_RANGE_TARGET) + 2) * 4);
@@ -1475,7 +1475,7 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
             } else {
                 const RxLists X = rx_lists(ctx, cur);
                 k_layer_begin<<<1, 128, 0, cs>>>(ctx->ctr, ctx->pop_delta);
-                CAPTURE_TRY(cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 4, cs));
+                CAPTURE_TRY(cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 2, cs));
                 k_rx_split<W, T><<<g_stream, 256, 0, cs>>>(X.src, X.done, X.act, ctx->cap, L.rx, ctx->ctr,
                                                            ctx->fcount, ctx->fshift);
                 CAPTURE_TRY(cudaGetLastError());

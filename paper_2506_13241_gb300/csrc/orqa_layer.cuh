@@ -45,6 +45,22 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int)(h >> fshift); }
 
+// Fine-bucket counts are 16-bit, two per 32-bit word (half the footprint of
+// the randomly addressed count array).  A bucket holds at most sub_max <= 512
+// strings in a valid pass; an increment that finds a count of 2^15 or more
+// raises ERR_BUCKET_OVERFLOW, so no count ever carries into its neighbour
+// unseen (every later kernel returns once the error is set).
+__device__ __forceinline__ int bucket_rank(uint32_t* counts, int b, Counters* ctr) {
+    const int sh = 16 * (b & 1);
+    const int old = (int)((atomicAdd(&counts[b >> 1], 1u << sh) >> sh) & 0xffffu);
+    if (old >= 0x8000) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
+    return old;
+}
+
+__device__ __forceinline__ int bucket_count(const uint32_t* counts, long long b) {
+    return (int)((counts[b >> 1] >> (16 * (b & 1))) & 0xffffu);
+}
+
 // ---------------------------------------------------------------------------
 // Entry split of a run (see the header comment): strings with F = 0 only
 // meet the truncation and go to the output list; the others go to the active
@@ -91,7 +107,7 @@ constexpr int SPLIT_ITEMS = 4;
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, StrList active, long long cap,
                                                   const __grid_constant__ RxRun run, Counters* ctr,
-                                                  int32_t* fcount, int fshift) {
+                                                  uint32_t* fcount, int fshift) {
     __shared__ int warp_tot[33];
     __shared__ unsigned long long s_base[2];
     if (block_aborted(ctr)) return;
@@ -167,7 +183,7 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
                 int pos[CHUNK_BITS], np, idx;
                 bool more;
                 const uint64_t h = unit_key_hash<W>(x, z[k], run.mask, 0, pos, np, idx, more, pid);
-                const int rk = atomicAdd(&fcount[fine_bucket(h, fshift)], 1);
+                const int rk = bucket_rank(fcount, fine_bucket(h, fshift), ctr);
                 if (slot < cap) {
                     active.h[slot] = h;
                     active.rank[slot] = rk;
@@ -206,7 +222,7 @@ __global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHan
 // then offsets[b]; offsets[n] = total.
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int32_t* counts, long long* offsets,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* counts, long long* offsets,
                                                              long long* tile_sums, const Counters* ctr) {
     if (block_aborted(ctr)) return;
     __shared__ int warp_tot[33];
@@ -214,7 +230,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int32_t* coun
     int v[SCAN_ITEMS], s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = counts[base + k];
+        v[k] = bucket_count(counts, base + k);
         s += v[k];
     }
     int total;
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums,
 // end offsets[n] = total closes the last ranges, and range_start[J] = n for
 // J = ceil(total / T).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, const long long* tile_sums,
-                                                           const int32_t* counts, long long n,
+                                                           const uint32_t* counts, long long n,
                                                            int32_t* range_start, long long T,
                                                            const Counters* ctr) {
     if (block_aborted(ctr)) return;
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, c
     const long long add = tile_sums[blockIdx.x];
     const long long total = tile_sums[SCAN_TILE];
     const long long J = (total + T - 1) / T;
-    long long prev = (base == 0) ? -1 : offsets[base] + add - counts[base - 1];
+    long long prev = (base == 0) ? -1 : offsets[base] + add - bucket_count(counts, base - 1);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const long long o = offsets[base + k] + add;
@@ -349,16 +365,16 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long cap, int fshift,
                                                         const long long* __restrict__ offsets, void* dst,
-                                                        int32_t* fcount, long long n_fine, Counters* ctr) {
+                                                        uint32_t* fcount, long long n_fine, Counters* ctr) {
     constexpr int RQ = record_bytes(W) / 16;  // 16-byte quarters per record
     __shared__ uint4 stage[256 / 32][32][RQ];
     if (block_aborted(ctr)) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const long long n = min((long long)ctr->n_active, cap);
     // the counts were consumed by the scan; clear them for the next pass
-    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < n_fine;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < n_fine / 2;
          b += (long long)gridDim.x * blockDim.x)
-        fcount[b] = 0;
+        fcount[b] = 0u;
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
     for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x;
          base - threadIdx.x < n; base += stride) {  // warp-uniform: all lanes iterate together
@@ -574,7 +590,7 @@ template <int W, typename T>
 __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const void* bk, const long long* __restrict__ offsets, const int32_t* __restrict__ range_start,
     long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
-    StrList next, long long cap, Counters* ctr, int32_t* fcount_next, int fshift, unsigned long long* pop_delta) {
+    StrList next, long long cap, Counters* ctr, uint32_t* fcount_next, int fshift, unsigned long long* pop_delta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LocalSmem<W, T>& S = *reinterpret_cast<LocalSmem<W, T>*>(smem_raw);
     if (block_aborted(ctr)) return;
@@ -887,7 +903,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 for (int j = 0; j < np2l; ++j) clear_bit<W>(x2, p2l[j]);
                 h = with_pid(hash_key<W>(zz, x2, ppl), ppl);
             }
-            const int rk = mr ? atomicAdd(&fcount_next[fine_bucket(h, fshift)], 1) : 0;
+            const int rk = mr ? bucket_rank(fcount_next, fine_bucket(h, fshift), ctr) : 0;
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, zz);
