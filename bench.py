@@ -239,15 +239,24 @@ def run_gpu(args, wl, rank, world):
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
         e2e_updates += upd
-    times = [total_ms, e2e_s]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor(times, dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.tolist()
-    return dict(total_ms=times[0], updates=total_updates, mags=mags, peak=peak, clocks=clk,
-                prof=prof, e2e_s=times[1], e2e_updates=e2e_updates, h2d=h2d, d2h=d2h,
+    times, sums = reduce_over_ranks([total_ms, e2e_s], [total_updates, e2e_updates], "cuda")
+    return dict(total_ms=times[0], updates=sums[0], mags=mags, peak=peak, clocks=clk,
+                prof=prof, e2e_s=times[1], e2e_updates=sums[1], h2d=h2d, d2h=d2h,
                 capacity=capacity, fp64_ops=fp64_ops)
+
+
+def reduce_over_ranks(times, counts, device="cpu"):
+    """Replicas on N ranks: the slowest rank's times (max) and the work of
+    all ranks (sum).  One rank: unchanged."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(times), list(counts)
+    import torch
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), [int(round(v)) for v in c.tolist()]
 
 
 def fp64_entry(prof, fp64_ops, sm_mhz):
@@ -602,10 +611,10 @@ def main(argv=None):
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    total_updates = res["updates"] * world
+    total_updates = res["updates"]  # summed over the ranks' replicas
     secs = res["total_ms"] * 1e-3
     value = total_updates / secs
-    e2e_value = res["e2e_updates"] * world / res["e2e_s"]
+    e2e_value = res["e2e_updates"] / res["e2e_s"]
     launches = sum(p["launches"] for p in res["prof"]) + sum(
         p["launches"] for p in res["prof"] if p["name"] == "expect")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
