@@ -378,6 +378,40 @@ __device__ __forceinline__ int chunk_positions(const uint64_t (&f)[W], int skip,
     return r;
 }
 
+// Positions (ascending) of the set bits of f whose rank is in
+// [skip, skip + CHUNK_BITS) (pos, the count is returned) and in
+// [skip + CHUNK_BITS, skip + 2 CHUNK_BITS) (pos2, np2), in one sweep.
+template <int W>
+__device__ __forceinline__ int chunk_positions2(const uint64_t (&f)[W], int skip, int (&pos)[CHUNK_BITS],
+                                                int (&pos2)[CHUNK_BITS], int& np2) {
+    int r = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t v = f[w];
+        if (r == 2 * CHUNK_BITS) break;
+        const int cnt = __popcll(v);
+        if (skip >= cnt) {
+            skip -= cnt;
+            continue;
+        }
+        if (skip > 0) {
+            v &= ~((1ull << nth_set_bit(v, skip)) - 1ull);
+            skip = 0;
+        }
+        while (v != 0 && r < 2 * CHUNK_BITS) {
+            const int p = 64 * w + (__ffsll((long long)v) - 1);
+            if (r < CHUNK_BITS)
+                pos[r] = p;
+            else
+                pos2[r - CHUNK_BITS] = p;
+            ++r;
+            v &= v - 1;
+        }
+    }
+    np2 = r > CHUNK_BITS ? r - CHUNK_BITS : 0;
+    return r < CHUNK_BITS ? r : CHUNK_BITS;
+}
+
 // Unit key of a string for chunk pass `pass` of an X-rotation run: z and x
 // with the chunk's bits cleared (see the unit definition in the layer
 // kernels).  Returns its 64-bit hash; fills the chunk's qubit positions,

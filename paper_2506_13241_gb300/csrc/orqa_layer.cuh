@@ -467,7 +467,7 @@ struct LocalSmem {
     uint64_t sz[W][LB_MAX];
     T sc[LB_MAX];
     T dense[LB_RU][32];         // unit rows (slot = chunk bits)
-    int32_t table[LB_TABLE];
+    uint16_t table[LB_TABLE];   // hash table of string indices (0xffff: empty)
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
     int16_t rep_uid[LB_MAX];    // unit id of a representative
@@ -479,6 +479,7 @@ struct LocalSmem {
     uint16_t list1[LB_WARPS][LB_LIST];
     uint16_t list2[LB_WARPS][LB_LIST];
     Rot<T> hrot[LB_RU];         // cos and sin of the current level's gate, per unit
+    Rot<T> srot[MAX_QUBITS];    // cos and sin per qubit (contexts with one problem)
     uint8_t s_idx[LB_MAX];
     int blk_delta[MAX_QUBITS];
     int warp_tot[33];
@@ -599,7 +600,11 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const int pass = ctr->pass;
     const long long J = (offsets[n_fine] + range_target - 1) / range_target;
 
-    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) S.blk_delta[t] = 0;
+    const bool batched = run.tab.f64 != nullptr;
+    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) {
+        S.blk_delta[t] = 0;
+        S.srot[t] = Coef<T>::rot(run, 0u, t);  // one read of the parameter table per qubit
+    }
     unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
     // The work items are sub-ranges; the next one (claiming a new range when
     // the current range is done) is prepared by warp LB_WARPS - 1 while the
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         S.cur = S.nx;
         S.n_units = 0;
     }
-    for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = -1;
+    for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = 0xffffu;
     for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.rep_cnt[t] = 0;
     __syncthreads();
     if (S.cur.rj >= J) break;
@@ -661,8 +666,9 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         int slot = S.s_unit[i];
         int rep = i;
         for (int probe = 0; probe < LB_TABLE; ++probe) {  // 2*LB_MAX slots: never full
-            const int v = atomicCAS(&S.table[slot], -1, i);
-            if (v == -1) break;
+            const unsigned short old = atomicCAS(&S.table[slot], (unsigned short)0xffffu, (unsigned short)i);
+            if (old == 0xffffu) break;
+            const int v = old;
             bool eq = S.spid[v] == pi;
 #pragma unroll
             for (int w = 0; w < W; ++w) eq = eq && (S.sz[w][v] == z[w]) && (S.sx[w][v] == xb[w]);
@@ -749,12 +755,9 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 xn[w] = xb[w];
                 f[w] = z[w] & run.mask[w];
             }
-            np = chunk_positions<W>(f, CHUNK_BITS * pass, pos, more);
-            if (more) {
-                bool m2;
-                np2 = chunk_positions<W>(f, CHUNK_BITS * (pass + 1), pos2, m2);
-                for (int j = 0; j < np2; ++j) clear_bit<W>(xn, pos2[j]);
-            }
+            np = chunk_positions2<W>(f, CHUNK_BITS * pass, pos, pos2, np2);
+            more = np2 > 0;
+            for (int j = 0; j < np2; ++j) clear_bit<W>(xn, pos2[j]);
         }
         if (lane < LB_UPW) S.occ[ub + lane] = 0u;
         __syncwarp();
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 sgl = lo ^ hi;
                 dbl = lo & hi;
                 pop_before = __popc(o);
-                S.hrot[ub + lane] = Coef<T>::rot(run, upid, pos[j]);
+                S.hrot[ub + lane] = batched ? Coef<T>::rot(run, upid, pos[j]) : S.srot[pos[j]];
             }
             unsigned tot;
             unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
