@@ -159,7 +159,7 @@ def make_gpu_runner(wl, capacity, profile=True, fp32=False):
     c_p = torch.from_numpy(c_h).pin_memory()
     delta = wl["delta"]
 
-    fp64 = {"one": 0, "two": 0}
+    fp64 = {"one": 0, "two": 0, "branch": 0}  # pair updates and branch events of the timed steps
 
     def evolve():
         updates, mags, peak = 0, [], 0
@@ -171,6 +171,7 @@ def make_gpu_runner(wl, capacity, profile=True, fp32=False):
                 peak = max(peak, s["last_layer_peak"])
                 fp64["one"] += s["pair_updates_one"]
                 fp64["two"] += s["pair_updates_two"]
+                fp64["branch"] += s["branch_events"]
             mags.append(B.orqa_expect(ctx.ctx))
         return updates, mags, peak
 
@@ -206,7 +207,7 @@ def run_gpu(args, wl, rank, world):
         step_dev()
     torch.cuda.synchronize()
     ctx.profile_reset()
-    fp64["one"] = fp64["two"] = 0
+    fp64["one"] = fp64["two"] = fp64["branch"] = 0
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -242,7 +243,7 @@ def run_gpu(args, wl, rank, world):
     times, sums = reduce_over_ranks([total_ms, e2e_s], [total_updates, e2e_updates], "cuda")
     return dict(total_ms=times[0], updates=sums[0], mags=mags, peak=peak, clocks=clk,
                 prof=prof, e2e_s=times[1], e2e_updates=sums[1], h2d=h2d, d2h=d2h,
-                capacity=capacity, fp64_ops=fp64_ops)
+                capacity=capacity, fp64_ops=fp64_ops, branch_events=fp64["branch"])
 
 
 def reduce_over_ranks(times, counts, device="cpu"):
@@ -348,9 +349,28 @@ def oracle_sample(wl, seconds: float):
     return updates, time.perf_counter() - t0, steps, 0, mags
 
 
+def host_cpu():
+    """The host's CPU model (x86 'model name', else the Arm part fields) and
+    logical core count."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "CPU part"):
+            vals = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(key)]
+            if vals:
+                model = vals[0] if key == "model name" else "Arm CPU part %s" % vals[0]
+                break
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_baseline(wl, seconds):
     upd, secs, steps, partial, mags = oracle_sample(wl, seconds)
     return {"value": upd / secs if secs > 0 else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": "first %d of %d time steps of %s plus %d gates of the next (%d string-gate "
                       "updates, %.1f s)" % (steps, wl["steps"], wl["name"], partial, upd, secs),
             "magnetization": mags}
@@ -376,7 +396,7 @@ def run_reference(args, wl):
             "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(wl),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": "first %d of %d time steps of %s plus %d gates, per step" % (
                                  steps, wl["steps"], wl["name"], partial)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -640,6 +660,8 @@ def main(argv=None):
             "gpu_launches": launches, "clocks": res["clocks"],
             "magnetization": res["mags"], "peak_strings": res["peak"], "capacity": res["capacity"]}
     line["fp64"] = fp64_entry(res["prof"], res["fp64_ops"], res["clocks"].get("sm_mhz"))
+    # secondary metric: anticommuting (string, gate) pairs per second (rank 0's replica)
+    line["branch_events_per_s"] = res["branch_events"] / (res["total_ms"] * 1e-3) * world
     if args.precision == "fp32":
         # The precision form's error per step against the GPU FP64 path on
         # the same workload (one untimed evolution after the timed run).
