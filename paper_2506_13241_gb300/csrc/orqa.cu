@@ -80,7 +80,7 @@ struct orqa_ctx {
     std::vector<CachedProgram> programs;
     double* prog_results = nullptr;
     ProgramStats* prog_stats = nullptr;
-    long long* foffsets = nullptr;
+    uint32_t* foffsets = nullptr;
     long long* tile_sums = nullptr;
     int32_t* range_start = nullptr;    // first bucket of each unit-kernel range
     uint64_t* hash_active = nullptr;   // unit-key hashes of the active list
@@ -205,7 +205,7 @@ Layout layout(int n_qubits, long long cap, int P) {
     t += 3 * (2 * L.str_x + L.str_c + L.str_pid);  // three string buffers
     t += L.shared;                         // layer / merge scratch
     t += align_up(F * 2);                  // fine counts (16 bits each)
-    t += align_up((F + 1) * 8);            // fine offsets
+    t += align_up((F + 1) * 4);            // fine offsets (32-bit)
     t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
     t += align_up(((size_t)(cap / MIN_RANGE_TARGET) + 2) * 4);  // unit-kernel range starts
     t += align_up(sizeof(Counters));
@@ -1092,7 +1092,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->n_fine = (int)fine_buckets(cfg->capacity, ctx->bucket_density);
     ctx->fshift = 64 - __builtin_ctzll((unsigned long long)ctx->n_fine);
     ctx->fcount = (uint32_t*)p; p += align_up(F * 2);
-    ctx->foffsets = (long long*)p; p += align_up((F + 1) * 8);
+    ctx->foffsets = (uint32_t*)p; p += align_up((F + 1) * 4);
     ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
     ctx->range_start = (int32_t*)p; p += align_up(((size_t)(cfg->capacity / MIN_RANGE_TARGET) + 2) * 4);
     ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));

@@ -219,10 +219,12 @@ __global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHan
 // ---------------------------------------------------------------------------
 // Exclusive scan of the fine-bucket counts (n = number of buckets, a
 // multiple of SCAN_TILE): tile sums, a one-block scan of the tile sums,
-// then offsets[b]; offsets[n] = total.
+// then offsets[b]; offsets[n] = total.  Offsets are 32-bit (every total is
+// at most the capacity, < 2^31), which halves the table the scatter gathers
+// from at random.
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* counts, long long* offsets,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* counts, uint32_t* offsets,
                                                              long long* tile_sums, const Counters* ctr) {
     if (block_aborted(ctr)) return;
     __shared__ int warp_tot[33];
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* cou
     int run = block_scan_exclusive(s, warp_tot, total);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        offsets[base + k] = run;
+        offsets[base + k] = (uint32_t)run;
         run += v[k];
     }
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(long long* tile_sums,
 // first bucket exactly for the j with offsets[b-1] < j*T <= offsets[b]; the
 // end offsets[n] = total closes the last ranges, and range_start[J] = n for
 // J = ceil(total / T).
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, const long long* tile_sums,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(uint32_t* offsets, const long long* tile_sums,
                                                            const uint32_t* counts, long long n,
                                                            int32_t* range_start, long long T,
                                                            const Counters* ctr) {
@@ -283,18 +285,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(long long* offsets, c
     const long long add = tile_sums[blockIdx.x];
     const long long total = tile_sums[SCAN_TILE];
     const long long J = (total + T - 1) / T;
-    long long prev = (base == 0) ? -1 : offsets[base] + add - bucket_count(counts, base - 1);
+    long long prev = (base == 0) ? -1 : (long long)offsets[base] + add - bucket_count(counts, base - 1);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        const long long o = offsets[base + k] + add;
-        offsets[base + k] = o;
+        const long long o = (long long)offsets[base + k] + add;
+        offsets[base + k] = (uint32_t)o;
         const long long jlo = (prev < 0) ? 0 : prev / T + 1;
         const long long jhi = min(o / T, J - 1);
         for (long long j = jlo; j <= jhi; ++j) range_start[j] = (int32_t)(base + k);
         prev = o;
     }
     if (base + SCAN_ITEMS == n) {  // the end bucket boundary
-        offsets[n] = total;
+        offsets[n] = (uint32_t)total;
         for (long long j = prev / T + 1; j <= J - 1; ++j) range_start[j] = (int32_t)n;
         range_start[J] = (int32_t)n;
     }
@@ -364,7 +366,7 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 // records instead of 32 scattered 16-byte pieces.
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long cap, int fshift,
-                                                        const long long* __restrict__ offsets, void* dst,
+                                                        const uint32_t* __restrict__ offsets, void* dst,
                                                         uint32_t* fcount, long long n_fine, Counters* ctr) {
     constexpr int RQ = record_bytes(W) / 16;  // 16-byte quarters per record
     __shared__ uint4 stage[256 / 32][32][RQ];
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
         }
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k)
-            if (slot[k] >= 0) slot[k] += offsets[fine_bucket(h[k], fshift)];
+            if (slot[k] >= 0) slot[k] += (long long)offsets[fine_bucket(h[k], fshift)];
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
@@ -467,7 +469,7 @@ struct LocalSmem {
     uint64_t sz[W][LB_MAX];
     T sc[LB_MAX];
     T dense[LB_RU][32];         // unit rows (slot = chunk bits)
-    uint16_t table[LB_TABLE];   // hash table of string indices (0xffff: empty)
+    alignas(4) uint16_t table[LB_TABLE];  // hash table of string indices (0xffff: empty), then unit masks
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
     int16_t rep_uid[LB_MAX];    // unit id of a representative
@@ -530,7 +532,7 @@ __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned v, unsigned& to
 // (a range can span many empty buckets when few strings are active).
 template <typename Smem>
 __device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int32_t* __restrict__ range_start,
-                                              const long long* __restrict__ offsets, long long J, int sub_max,
+                                              const uint32_t* __restrict__ offsets, long long J, int sub_max,
                                               bool first) {
     const int lane = threadIdx.x & 31;
     int rj, b_lo, b_end;
@@ -554,12 +556,12 @@ __device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int3
         if (lane == 0) S.nx.rj = rj;
         return;
     }
-    const long long base = offsets[b_lo];
+    const long long base = (long long)offsets[b_lo];
     int lo = b_lo, hi = b_end;  // lo qualifies; the answer lies in [lo, hi]
     while (lo < hi) {           // warp-uniform
         const long long span = hi - lo;
         const int cand = lo + (int)((span * (lane + 1) + 31) >> 5);  // nondecreasing, last = hi
-        const unsigned bal = __ballot_sync(FULL_MASK, offsets[cand] - base <= sub_max);
+        const unsigned bal = __ballot_sync(FULL_MASK, (long long)offsets[cand] - base <= sub_max);
         const int K = __popc(bal);
         if (K == 32) {
             lo = hi;
@@ -570,7 +572,7 @@ __device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int3
         if (K > 0) lo = last_good;
         hi = first_bad - 1;
     }
-    const long long end = offsets[lo];
+    const long long end = (long long)offsets[lo];
     if (lane == 0) {
         S.nx.rj = rj;
         S.nx.b_lo = b_lo;
@@ -589,7 +591,7 @@ __device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int3
 // most sub_max / LB_TABLE).
 template <int W, typename T>
 __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
-    const void* bk, const long long* __restrict__ offsets, const int32_t* __restrict__ range_start,
+    const void* bk, const uint32_t* __restrict__ offsets, const int32_t* __restrict__ range_start,
     long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
     StrList next, long long cap, Counters* ctr, uint32_t* fcount_next, int fshift, unsigned long long* pop_delta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -598,7 +600,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const unsigned long long dbits = Coef<T>::threshold(run);
     const int pass = ctr->pass;
-    const long long J = (offsets[n_fine] + range_target - 1) / range_target;
+    const long long J = ((long long)offsets[n_fine] + range_target - 1) / range_target;
 
     const bool batched = run.tab.f64 != nullptr;
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) {
@@ -715,6 +717,9 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             S.group_cursor = 0;
         }
     }
+    // occupancy masks of the units, in the hash table's storage (free now)
+    uint32_t* uocc = reinterpret_cast<uint32_t*>(S.table);
+    for (int u = tid; u < n_units; u += LB_THREADS) uocc[u] = 0u;
     __syncthreads();
     for (int i = tid; i < m; i += LB_THREADS) {
         const int r = S.s_unit[i];
@@ -722,6 +727,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         const int k = ((atomicSub(&S.rep_cnt[r >> 1], 1 << (16 * (r & 1))) >> (16 * (r & 1))) & 0xffff) - 1;
         S.s_order[S.ustart[u] + k] = (int16_t)i;
         S.s_unit[i] = (int16_t)u;
+        atomicOr(&uocc[u], 1u << S.s_idx[i]);
     }
     __syncthreads();
 
@@ -759,18 +765,14 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             more = np2 > 0;
             for (int j = 0; j < np2; ++j) clear_bit<W>(xn, pos2[j]);
         }
-        if (lane < LB_UPW) S.occ[ub + lane] = 0u;
-        __syncwarp();
+        if (lane < LB_UPW) S.occ[ub + lane] = own ? uocc[u] : 0u;
         // strings of this warp's units into their slots (a contiguous run of
         // the unit-ordered list)
         {
             const int k_lo = S.ustart[g], k_hi = S.ustart[min(g + LB_UPW, n_units)];
             for (int k = k_lo + lane; k < k_hi; k += 32) {
                 const int i = S.s_order[k];
-                const int ul = S.s_unit[i] - g;
-                const int l = S.s_idx[i];
-                S.dense[ub + ul][l] = S.sc[i];
-                atomicOr(&S.occ[ub + ul], 1u << l);
+                S.dense[ub + S.s_unit[i] - g][S.s_idx[i]] = S.sc[i];
             }
         }
         __syncwarp();
