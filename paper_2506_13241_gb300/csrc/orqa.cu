@@ -1242,8 +1242,7 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
     const double dabs = ctx->relative ? 0.0 : delta;
     orqa_status st = ORQA_DISPATCH(ctx, merge_state, ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m);
     if (st != ORQA_OK) return st;
-    ctx->cur = dst;
-    ctx->n = m;
+    if ((st = host_commit(ctx, dst, m)) != ORQA_OK) return st;
     if (ctx->relative) {
         long long dropped = 0;
         st = ORQA_DISPATCH(ctx, truncate_relative, ctx, delta, &dropped);

@@ -252,6 +252,16 @@ def test_merge_truncate_and_duplicates(orqa, oracle_mod):
     ctx.merge_truncate(1e-3)
     op.truncate(1e-3)
     assert_bit_exact(gpu_canonical(ctx, n), oracle_canonical(op, n), "truncate")
+    # the merged operator is the committed one for the device-side counts of
+    # the next layers and of the expectation
+    assert abs(ctx.expect() - op.expect_zero()) < M_TOL
+    for layer in ([("rzz", 3, 7, -math.pi / 2), ("rzz", 1, 12, -math.pi / 2)],
+                  [("rx", q, None, 0.7) for q in (2, 5, 9, 13)]):
+        ctx.apply_layer(layer, 1e-3)
+        for g in layer:
+            op.apply(g, 1e-3)
+        assert_bit_exact(gpu_canonical(ctx, n), oracle_canonical(op, n), "layer after merge")
+    assert abs(ctx.expect() - op.expect_zero()) < M_TOL
 
 
 def test_empty_operator(orqa):
