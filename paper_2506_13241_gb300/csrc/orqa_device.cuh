@@ -176,10 +176,6 @@ __device__ __forceinline__ void store_plane(uint64_t* p, long long i, const uint
     }
 }
 
-__device__ __forceinline__ int get_bit(const uint64_t* v, int q) {
-    return (int)((v[q >> 6] >> (q & 63)) & 1ull);
-}
-
 // Register-only bit access for W-word planes (no dynamic array indexing, so
 // the planes stay in registers).
 // v >> d and v << d on W-word planes, 0 < d < 64 W.
@@ -220,19 +216,6 @@ __device__ __forceinline__ int bit_of(const uint64_t (&v)[W], int q) {
     } else {
         const uint64_t w = (q < 64) ? v[0] : v[1];
         return (int)((w >> (q & 63)) & 1ull);
-    }
-}
-
-template <int W>
-__device__ __forceinline__ void xor_bit(uint64_t (&v)[W], int q) {
-    if constexpr (W == 1) {
-        v[0] ^= 1ull << q;
-    } else {
-        const uint64_t b = 1ull << (q & 63);
-        if (q < 64)
-            v[0] ^= b;
-        else
-            v[1] ^= b;
     }
 }
 
@@ -450,24 +433,6 @@ __device__ __forceinline__ long long warp_append(bool pred, unsigned long long* 
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
 }
 
-// Truncation test of Algorithm 1 (keep iff c != 0 and |c| >= delta) done on
-// the IEEE bit patterns: for non-negative doubles the magnitude order is the
-// unsigned integer order of (bits & 0x7fff...), so this is exact and costs
-// no FP64 instruction (FP64 issue rate is the scarce resource on GB300).
-// delta_bits is the bit pattern of delta >= 0.
-__device__ __forceinline__ bool keep_bits(double v, unsigned long long delta_bits) {
-    const unsigned long long m = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-    return m != 0ull && m >= delta_bits;
-}
-
-__device__ __forceinline__ bool keep_coef(double v, double delta) {
-    return keep_bits(v, (unsigned long long)__double_as_longlong(delta));
-}
-
-__device__ __forceinline__ bool nonzero_bits(double v) {
-    return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
-}
-
 // Coefficient types: FP64 (the default) and FP32 (ORQA_FLAG_FP32).  Zero and
 // threshold tests are integer tests on the magnitude bits of the stored
 // type; thresholds arrive as magnitude bits of that type.
@@ -485,7 +450,6 @@ struct Coef<double> {
     __device__ static unsigned long long to_slot(double v) { return (unsigned long long)__double_as_longlong(v); }
     __device__ static double from_slot(unsigned long long b) { return __longlong_as_double((long long)b); }
     __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits64; }
-    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
     // (cos, sin) of problem p's angle on qubit q
     __device__ static Rot<double> rot(const RxRun& r, unsigned p, int q) {
         if (r.tab.f64) {
@@ -503,7 +467,6 @@ struct Coef<float> {
     __device__ static unsigned long long to_slot(float v) { return (unsigned long long)__float_as_uint(v); }
     __device__ static float from_slot(unsigned long long b) { return __uint_as_float((unsigned)b); }
     __device__ static unsigned long long threshold(const RxRun& r) { return r.dbits32; }
-    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
     __device__ static Rot<float> rot(const RxRun& r, unsigned p, int q) {
         if (r.tab.f32) {
             const float4 v = r.tab.f32[p * MAX_QUBITS + q];
@@ -513,15 +476,15 @@ struct Coef<float> {
     }
 };
 
+// Truncation test of Algorithm 1 (keep iff c != 0 and |c| >= delta) on the
+// IEEE bit patterns: for non-negative values the magnitude order is the
+// unsigned order of the magnitude bits, so the test is exact and uses no
+// floating-point instruction (FP64 issue is the scarce resource on GB300).
+// tbits: the threshold as magnitude bits of T.
 template <typename T>
 __device__ __forceinline__ bool keep_t(T v, unsigned long long tbits) {
     const unsigned long long m = Coef<T>::mag(v);
     return m != 0ull && m >= tbits;
-}
-
-template <typename T>
-__device__ __forceinline__ bool nonzero_t(T v) {
-    return Coef<T>::mag(v) != 0ull;
 }
 
 // a*b + c*d (+ a small correction `extra`) in FP32 with the compensated
