@@ -171,3 +171,39 @@ def test_program_capacity_error_keeps_last_layer(orqa):
     assert e.value.status == orqa.ORQA_ECAPACITY
     assert_bit_exact(gpu_canonical(ctx, n), gpu_canonical(ref, n), "state after the failing layer")
     assert abs(ctx.expect() - ref.expect()) < M_TOL
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_batched_program_one_word_planes(orqa, oracle_mod, fp32):
+    """A batched program on 40 qubits (one 64-bit word per plane): random
+    edges with a Clifford ZZ layer and X layers with per-problem angles;
+    FP64 bit-exact per problem, FP32 within 1e-6 of the oracle."""
+    import random
+    rng = random.Random(4040)
+    n = 40
+    edges = set()
+    while len(edges) < 45:
+        a, b = rng.sample(range(n), 2)
+        edges.add((min(a, b), max(a, b)))
+    edges = sorted(edges)
+    thetas = [0.0, 0.4, math.pi / 4, 1.1, math.pi / 2]
+    obs = [W.z_label(n, [7]), W.z_label(n, [3, 20, 33])]
+    problems = [[(lab, 1.0)] for th in thetas for lab in obs]
+    theta_p = [th for th in thetas for _ in obs]
+    P = len(problems)
+    zz = [("rzz", a, b, -math.pi / 2) for a, b in edges]
+    xx = [("rx", q, None, 0.3) for q in range(n)]
+    theta = np.array([[theta_p[p]] * n for p in range(P)])
+    ctx = orqa.Context(n, 1 << 22, problems=P, fp32=fp32)
+    prog = ctx.program([(zz, False, None), (xx, True, theta)])
+    ctx.set_labels_batch(problems)
+    mags = ctx.run_program(prog, 3, 1e-4)
+    sets = batch_sets(ctx, n, P)
+    for p in range(P):
+        layers = [zz, [("rx", q, None, theta_p[p]) for q in range(n)]]
+        mo, op = oracle_mod.run_layers(n, problems[p], layers, 3, 1e-4)
+        if fp32:
+            assert np.max(np.abs(mags[:, p] - np.array(mo))) < 1e-6, p
+        else:
+            assert np.max(np.abs(mags[:, p] - np.array(mo))) < M_TOL, p
+            assert_bit_exact(sets[p], oracle_canonical(op, n), "problem %d" % p)
