@@ -92,3 +92,40 @@ def test_label_encoding_matches_paper_codes():
     x, z = orqa.strings_from_labels(["IXYZ" * 20], 80)
     codes = planes_to_codes(x, z, 80)
     assert list(codes[0][:4]) == [0, 1, 2, 3]
+
+
+def test_null_context_is_rejected_before_any_cuda_call(lib):
+    """Every entry point that takes a context returns ORQA_EINVAL for a null
+    one, without touching CUDA."""
+    E = orqa.ORQA_EINVAL
+    n = ctypes.c_int64()
+    d = ctypes.c_double()
+    t = orqa.orqa_tuning()
+    g = (orqa.orqa_gate * 1)()
+    desc = (orqa.orqa_layer_desc * 1)()
+    buf = (ctypes.c_uint64 * 4)()
+    assert lib.orqa_set_operator(None, 0, None, None, None) == E
+    assert lib.orqa_set_operator_batch(None, 0, None, None, None, None) == E
+    assert lib.orqa_apply_layer(None, g, 1, 0.0, ctypes.byref(n)) == E
+    assert lib.orqa_apply_layer_batch(None, g, 1, None, 0.0, ctypes.byref(n)) == E
+    assert lib.orqa_apply_pauli_rotation(None, buf, buf, 0.1, 0.0, ctypes.byref(n)) == E
+    assert lib.orqa_merge_truncate(None, 0.0, ctypes.byref(n)) == E
+    assert lib.orqa_expect(None, ctypes.byref(d)) == E
+    assert lib.orqa_expect_batch(None, ctypes.byref(d)) == E
+    assert lib.orqa_problem_sizes(None, ctypes.byref(n)) == E
+    assert lib.orqa_histogram(None, 4, -2.0, ctypes.byref(n), None) == E
+    assert lib.orqa_run_program(None, desc, 1, 1, 0.0, None, 0) == E
+    assert lib.orqa_get_tuning(None, ctypes.byref(t)) == E
+    assert lib.orqa_set_tuning(None, ctypes.byref(t)) == E
+    assert lib.orqa_autotune(None, desc, 1, 1, 0.0, 1, ctypes.byref(t), None) == E
+    assert lib.orqa_stats(None, None) == E
+    assert lib.orqa_profile(None, 0, None) == E
+
+
+def test_noalloc_rejects_bad_sizes_before_any_cuda_call(lib):
+    d = ctypes.c_double()
+    assert lib.orqa_expect_noalloc(0, 1, None, None, ctypes.byref(d), None) == orqa.ORQA_EINVAL
+    assert lib.orqa_expect_noalloc(127, -1, None, None, ctypes.byref(d), None) == orqa.ORQA_EINVAL
+    assert lib.orqa_expect_noalloc(127, orqa.ORQA_NOALLOC_MAX_STRINGS + 1, None, None, ctypes.byref(d),
+                                   None) == orqa.ORQA_ECAPACITY
+    assert lib.orqa_expect_noalloc(127, 5, None, None, ctypes.byref(d), None) == orqa.ORQA_EINVAL
