@@ -1,0 +1,52 @@
+"""Host-side pieces of bench.py that need no GPU: argument defaults, the
+roofline entry, the kernel-launch count, error summaries and workload
+names."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_defaults_finish_within_minutes():
+    a = bench.parse_args([])
+    assert (a.gpus, a.steps, a.warmup) == (1, 3, 3)
+    assert a.warmup >= 3 and a.workload == bench.DEFAULT_WORKLOAD and a.impl == "orqa"
+
+
+def test_roofline_entry_uses_the_dominant_kernel():
+    prof = [{"name": "unit_local", "launches": 4, "ms": 40.0, "bytes": 4.0e10},
+            {"name": "bucket_scatter", "launches": 4, "ms": 10.0, "bytes": 2.0e10},
+            {"name": "expect", "launches": 0, "ms": 0.0, "bytes": 0.0}]
+    r = bench.roofline_entry(prof, 1, bench.DEFAULT_WORKLOAD)
+    peak, _ = bench.measured_peaks()
+    assert r["kernel"] == "unit_local" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 1000.0) < 1e-9                     # 4e10 B / 40 ms
+    assert abs(r["frac"] - round(1000.0 / peak, 4)) < 1e-12
+    assert r["traffic"] == bench.MEASURED_TRAFFIC[(bench.DEFAULT_WORKLOAD, "unit_local")]
+    assert abs(r["share_of_kernel_time"] - 0.8) < 1e-12
+    assert bench.roofline_entry(prof, 1, "chain12")["traffic"] is None
+
+
+def test_kernel_launch_count():
+    prof = [{"name": "rzz_layer", "launches": 2}, {"name": "rx_split", "launches": 2},
+            {"name": "fine_scan", "launches": 5}, {"name": "bucket_scatter", "launches": 5},
+            {"name": "unit_local", "launches": 5}, {"name": "expect", "launches": 2},
+            {"name": "merge_assign", "launches": 1}, {"name": "merge_offsets", "launches": 1},
+            {"name": "merge_scatter", "launches": 1}, {"name": "merge_reduce", "launches": 1},
+            {"name": "truncate", "launches": 1}]
+    # 2 + 2 + 15 + 5 + 5 + 4 + 4 merge + 1 truncate, + (2 + 5) pass bookkeeping, + (2 + 1 + 1) commits
+    assert bench.kernel_launches(prof) == 38 + 7 + 4
+
+
+def test_error_entry_and_names():
+    e = bench.error_entry([1.0, 0.5, 0.25], [1.0, 0.5 + 1e-9])
+    assert e["steps_compared"] == 2 and abs(e["max_abs"] - 1e-9) < 1e-15
+    wl = bench.sweep_from_name("sweep_n=4_t=2_delta=1e-3")
+    assert len(wl["problems"]) == 12 and wl["steps"] == 2 and wl["delta"] == 1e-3
+    cfg = bench.workload_config(bench.W.workload("heavyhex"), "fp32")
+    assert cfg["coefficients"] == "fp32" and cfg["n_qubits"] == 127 and "l2" in cfg
+    host = bench.host_cpu()
+    assert host["nproc"] >= 1 and host["model"]
