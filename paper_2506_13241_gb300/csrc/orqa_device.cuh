@@ -508,11 +508,6 @@ __device__ __forceinline__ float mul_pair(float hi, float lo, float v) {
 }
 
 // One-member pair (Eq. update_rule with the partner absent): (cos v, sin v).
-__device__ __forceinline__ void one_member(const Rot<double>& r, double v, double& pc, double& ps) {
-    pc = __dmul_rn(r.c, v);
-    ps = __dmul_rn(r.s, v);
-}
-
 __device__ __forceinline__ void one_member(const Rot<float>& r, float v, float& pc, float& ps) {
     pc = mul_pair(r.c, r.cl, v);
     ps = mul_pair(r.s, r.sl, v);
@@ -520,14 +515,42 @@ __device__ __forceinline__ void one_member(const Rot<float>& r, float v, float& 
 
 // Pair update of Eq. (update_rule) with both members present:
 // (c_Z, c_Y) -> (cos c_Z - sin c_Y, cos c_Y + sin c_Z).
-__device__ __forceinline__ void pair_update(const Rot<double>& r, double a, double b, double& na, double& nb) {
-    na = __dsub_rn(__dmul_rn(r.c, a), __dmul_rn(r.s, b));
-    nb = __dadd_rn(__dmul_rn(r.c, b), __dmul_rn(r.s, a));
-}
-
 __device__ __forceinline__ void pair_update(const Rot<float>& r, float a, float b, float& na, float& nb) {
     na = dot2f(r.c, a, -r.s, b, __fmaf_rn(r.cl, a, -__fmul_rn(r.sl, b)));
     nb = dot2f(r.c, b, r.s, a, __fmaf_rn(r.cl, b, __fmul_rn(r.sl, a)));
+}
+
+// One entry of a level's pair list, either case: u1 is the coefficient of
+// the present member (c_Z of a two-member pair), u2 that of the other
+// member (c_Y), or u1 again when the pair has one member; y_side says that
+// member is the sigma_y string.  Two members: (cos c_Z - sin c_Y,
+// cos c_Y + sin c_Z), every product and sum rounded once in that order.
+// One member: (cos c, sin c) at sigma_z, (-sin c, cos c) at sigma_y.  In
+// FP64, cos u1 and sin u2 serve both cases (a one-member pair needs exactly
+// those two products), so entries of both kinds share one pass of a list.
+__device__ __forceinline__ void pair_entry(const Rot<double>& r, double u1, double u2, bool two, bool y_side,
+                                           double& na, double& nb) {
+    const double p = __dmul_rn(r.c, u1), q = __dmul_rn(r.s, u2);
+    if (two) {
+        na = __dsub_rn(p, q);
+        nb = __dadd_rn(__dmul_rn(r.c, u2), __dmul_rn(r.s, u1));
+    } else {
+        // sigma_z present: (cos c, sin c); sigma_y present: (-sin c, cos c)
+        na = y_side ? Coef<double>::negate(q) : p;
+        nb = y_side ? p : q;
+    }
+}
+
+__device__ __forceinline__ void pair_entry(const Rot<float>& r, float u1, float u2, bool two, bool y_side,
+                                           float& na, float& nb) {
+    if (two) {
+        pair_update(r, u1, u2, na, nb);
+    } else {
+        float p, q;
+        one_member(r, u1, p, q);
+        na = y_side ? Coef<float>::negate(q) : p;
+        nb = y_side ? p : q;
+    }
 }
 
 }  // namespace orqa

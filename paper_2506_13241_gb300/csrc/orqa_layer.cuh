@@ -450,11 +450,12 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
 //     new c_Z = cos c_Z - sin c_Y,   new c_Y = cos c_Y + sin c_Z,
 // an absent member counting as 0 (Algorithm 1 inserts it), then the
 // truncation c == 0 or |c| < delta.  The pairs of a level (found with two
-// mask operations per unit) go to warp lists -- one member present: 2 DMUL,
-// both: 4 DMUL + 2 DADD -- processed by all lanes, and the outputs of a
-// group are enumerated one per lane.  FP64 instructions thus run on full
-// warps (GB300 issues FP64 at 2 lanes per clock per SM whatever the active
-// mask) and no lane loops over one unit's members.
+// mask operations per unit) go to one warp list -- the one-member pairs
+// (2 DMUL) first, then the two-member pairs (2 more DMUL + 2 DADD) --
+// processed by all lanes in one pass, and the outputs of a group are
+// enumerated one per lane.  FP64 instructions thus run on full warps
+// (GB300 issues FP64 at 2 lanes per clock per SM whatever the active mask)
+// and no lane loops over one unit's members.
 // ---------------------------------------------------------------------------
 // One work item of the unit kernel: buckets [b_lo, b_next) of range rj
 // (whose buckets end at b_end), holding strings [s0, s1) of the bucket order.
@@ -478,8 +479,7 @@ struct LocalSmem {
     int16_t ustart[LB_MAX + 1]; // first position of each unit in that order
     int32_t rep_cnt[LB_MAX / 2]; // strings per representative, two 16-bit counts per word
     uint16_t spid[LB_MAX];      // problem index of each string
-    uint16_t list1[LB_WARPS][LB_LIST];
-    uint16_t list2[LB_WARPS][LB_LIST];
+    uint16_t list[LB_WARPS][LB_LIST];  // pairs of the current level, per warp
     Rot<T> hrot[LB_RU];         // cos and sin of the current level's gate, per unit
     Rot<T> srot[MAX_QUBITS];    // cos and sin per qubit (contexts with one problem)
     uint8_t s_idx[LB_MAX];
@@ -795,45 +795,39 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             unsigned tot;
             unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
             const unsigned n1 = tot & 0xffffu, n2 = tot >> 16;
-            unsigned o1 = o12 & 0xffffu, o2 = o12 >> 16;
+            // one list per warp: the one-member pairs at [0, n1), the
+            // two-member pairs at [n1, n1 + n2); an entry is
+            // (lane << 6) | (sigma_y side of a lone member << 5) | slot
+            unsigned o1 = o12 & 0xffffu, o2 = n1 + (o12 >> 16);
             my_one += n1;
             my_two += n2;
-            for (unsigned b = sgl; b; b &= b - 1) {
+            for (unsigned b = sgl | dbl; b; b &= b - 1) {
                 const int l = __ffs(b) - 1;
-                S.list1[wp][o1++] = (uint16_t)((lane << 6) | (((hi >> l) & 1u) << 5) | l);
+                const bool d = (dbl >> l) & 1u;
+                S.list[wp][d ? o2 : o1] = (uint16_t)((lane << 6) | (d ? 0u : ((hi >> l) & 1u) << 5) | l);
+                o1 += d ? 0u : 1u;
+                o2 += d ? 1u : 0u;
             }
-            for (unsigned b = dbl; b; b &= b - 1) S.list2[wp][o2++] = (uint16_t)((lane << 5) | (__ffs(b) - 1));
             __syncwarp();
-            for (unsigned t = lane; t < n1; t += 32) {
-                const int e = S.list1[wp][t];
-                const int ur = ub + (e >> 6), la = e & 31, lb = la | bit;
+            for (unsigned t = lane; t < n1 + n2; t += 32) {
+                const bool two = t >= n1;
+                const int e = S.list[wp][t];
+                const int ur = ub + (e >> 6), la = e & 31;
                 const bool y_side = (e & 32) != 0;
-                const T v = S.dense[ur][y_side ? lb : la];
-                T p1, p2;
-                one_member(S.hrot[ur], v, p1, p2);
-                // sigma_z present: (cos c, sin c); sigma_y present: (-sin c, cos c)
-                const T na = y_side ? Coef<T>::negate(p2) : p1;
-                const T nb = y_side ? p1 : p2;
-                const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
-                my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
-                S.dense[ur][la] = na;
-                S.dense[ur][lb] = nb;
-                const unsigned keep = (ka ? (1u << la) : 0u) | (kb ? (1u << lb) : 0u);
-                const unsigned drop = ((1u << la) | (1u << lb)) & ~keep;
-                if (drop) atomicAnd(&S.occ[ur], ~drop);
-                if (keep) atomicOr(&S.occ[ur], keep);
-            }
-            for (unsigned t = lane; t < n2; t += 32) {
-                const int e = S.list2[wp][t];
-                const int ur = ub + (e >> 5), la = e & 31, lb = la | bit;
+                const int lb = la | bit;
+                const T u1 = S.dense[ur][y_side ? lb : la];
+                const T u2 = two ? S.dense[ur][lb] : u1;
                 T na, nb;
-                pair_update(S.hrot[ur], S.dense[ur][la], S.dense[ur][lb], na, nb);
+                pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
                 S.dense[ur][la] = na;
                 S.dense[ur][lb] = nb;
-                const unsigned drop = (ka ? 0u : (1u << la)) | (kb ? 0u : (1u << lb));
-                if (drop) atomicAnd(&S.occ[ur], ~drop);
+                // occupancy of the pair before (both, or the present member) and after
+                const unsigned was = two ? ((1u << la) | (1u << lb)) : (1u << (y_side ? lb : la));
+                const unsigned now = (ka ? (1u << la) : 0u) | (kb ? (1u << lb) : 0u);
+                if (was & ~now) atomicAnd(&S.occ[ur], ~(was & ~now));
+                if (now & ~was) atomicOr(&S.occ[ur], now & ~was);
             }
             __syncwarp();
             if (act) {
