@@ -120,8 +120,9 @@ def gate_index(gate, n: int) -> tuple:
     return index_from_codes(codes)
 
 
-def phase_exponent(I, J, n: int) -> int:
-    return _load().oracle_phase_exponent(_words(I), _words(J), n)
+def phase_exponent(I, J, n: int, lib_path: str | None = None) -> int:
+    """B(I, J) of Eq. (orqaproduct): sigma_I sigma_J = i^B sigma_{I xor J}."""
+    return _load(lib_path).oracle_phase_exponent(_words(I), _words(J), n)
 
 
 def rotation_cos_sin(theta: float):

@@ -55,6 +55,11 @@
 
 // The tests rebuild this file with ORACLE_MUTATION=k to plant one plausible
 // mistake and check that some pin fails; the default build plants none.
+//   1 source-indexed sign (Algorithm 1 as printed)   2 sin term from the updated value
+//   3 no exact Clifford angles                       4 sigma_y counted as diagonal
+//   5 exact zeros kept                               6 Levi-Civita orientation reversed
+//   7 commuting strings rotated too                  8 relative threshold from the max before the gate
+//   9 a branch overwrites an existing term           10 sin sign reversed at the Clifford angles
 #ifndef ORACLE_MUTATION
 #define ORACLE_MUTATION 0
 #endif
@@ -80,6 +85,7 @@ int local_code(const MultiIndex& I, int q) {
 int local_phase(int a, int b) {
     if (a == 0 || b == 0 || a == b) return 0;
     bool cyclic = (a == 1 && b == 2) || (a == 2 && b == 3) || (a == 3 && b == 1);
+    if (ORACLE_MUTATION == 6) cyclic = !cyclic;
     return cyclic ? 1 : -1;
 }
 
@@ -118,7 +124,7 @@ void rotation_cos_sin(double theta, double* c, double* s) {
         long long m = ((long long)k % 4 + 4) % 4;
         static const double cs[4][2] = {{1.0, 0.0}, {0.0, 1.0}, {-1.0, 0.0}, {0.0, -1.0}};
         *c = cs[m][0];
-        *s = cs[m][1];
+        *s = (ORACLE_MUTATION == 10) ? -cs[m][1] : cs[m][1];
         return;
     }
     *c = std::cos(theta);
@@ -142,8 +148,10 @@ double max_abs(const Operator* op) {
     return m;
 }
 
-void truncate_rel(Operator* op, double eps0) {
-    double thr = eps0 * max_abs(op);
+// Relative truncation of Eq. (truncation1): drops c == 0 and |c| <= eps0 * m,
+// m = max|c| over the operator after the gate's updates.
+void truncate_rel(Operator* op, double eps0, double m) {
+    double thr = eps0 * m;
     for (auto it = op->terms.begin(); it != op->terms.end();) {
         double v = it->second;
         if (v == 0.0 || std::fabs(v) <= thr)
@@ -160,7 +168,7 @@ void rotate(Operator* op, const MultiIndex& J, double theta) {
     std::vector<std::pair<MultiIndex, double>> updates;
     for (auto& kv : op->terms) {
         int B = phase_exponent(kv.first, J, op->n_qubits);
-        if (!is_odd(B)) continue;
+        if (ORACLE_MUTATION != 7 && !is_odd(B)) continue;
         double old = kv.second;
         kv.second = co * old;
         MultiIndex dest = xor_index(kv.first, J);
@@ -174,7 +182,7 @@ void rotate(Operator* op, const MultiIndex& J, double theta) {
         if (it == op->terms.end())
             op->terms.insert(u);
         else
-            it->second = it->second + u.second;
+            it->second = (ORACLE_MUTATION == 9) ? u.second : it->second + u.second;
     }
 }
 
@@ -216,8 +224,9 @@ void oracle_apply_gate(void* h, const uint64_t* J_words, double theta, double de
 void oracle_apply_gate_rel(void* h, const uint64_t* J_words, double theta, double eps0) {
     Operator* op = static_cast<Operator*>(h);
     MultiIndex J = {J_words[0], J_words[1], J_words[2], J_words[3]};
+    const double before = (ORACLE_MUTATION == 8) ? max_abs(op) : 0.0;
     rotate(op, J, theta);
-    truncate_rel(op, eps0);
+    truncate_rel(op, eps0, ORACLE_MUTATION == 8 ? before : max_abs(op));
 }
 
 // Gate without any truncation step (exact zeros are kept).

@@ -263,6 +263,42 @@ def test_truncation_drops_exactly_small_terms(oracle_mod):
                 assert lost == pytest.approx(sum(v * v for v in dropped.values()), abs=1e-15)
 
 
+def _relative_hand_cases(oracle_mod, lib_path=None):
+    """Hand examples of the relative rule of Eq. (truncation1): after a gate,
+    drop c == 0 and |c| <= eps0 * max|c|, the max taken over the operator
+    after that gate's updates.  Returns the three resulting operators as
+    {label: coefficient}."""
+    theta = math.atan2(0.8, 0.6)  # cos = 0.6, sin = 0.8 (to rounding)
+    rx = ("rx", 0, None, theta)
+    # (a) Z + 0.09 X under Rx: the max falls from 1 to 0.8, so with eps0 = 0.1
+    # the threshold is 0.08 after the gate (X kept) but 0.1 before it
+    a = oracle_mod.Oracle(1, lib_path)
+    a.add_label("Z", 1.0)
+    a.add_label("X", 0.09)
+    a.apply_rel(rx, 0.1)
+    # (b) a tie: Z + 0.5 I under a gate that commutes with both; eps0 = 0.5
+    # puts the threshold exactly at 0.5, and |c| <= threshold is dropped
+    b = oracle_mod.Oracle(1, lib_path)
+    b.add_label("Z", 1.0)
+    b.add_label("I", 0.5)
+    b.apply_rel(("pauli", oracle_mod.index_from_label("Z"), None, 0.7), 0.5)
+    # (c) Rx(pi/2) on Z: cos = 0 exactly, so Z is left with an exact zero
+    # (removed) and Y carries the whole coefficient
+    c = oracle_mod.Oracle(1, lib_path)
+    c.add_label("Z", 1.0)
+    c.apply_rel(("rx", 0, None, math.pi / 2), 1e-3)
+    return [labels_dict(op, 1) for op in (a, b, c)]
+
+
+def test_relative_truncation_hand_examples(oracle_mod):
+    a, b, c = _relative_hand_cases(oracle_mod)
+    assert set(a) == {"Z", "Y", "X"}
+    assert a["X"] == 0.09
+    assert abs(a["Z"] - 0.6) < 1e-15 and abs(abs(a["Y"]) - 0.8) < 1e-15
+    assert b == {"Z": 1.0}
+    assert set(c) == {"Y"} and abs(c["Y"]) == 1.0
+
+
 def test_support_stays_in_light_cone(oracle_mod):
     n, edges = W.heavy_hex_eagle()
     _, dist = W.bfs_order(n, edges, 62)
@@ -312,36 +348,111 @@ def test_colouring_and_lattice():
 # Planted mistakes: each one must make some pin above fail.
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5])
-def test_planted_mistakes_are_caught(oracle_mod, tmp_path, mutation):
-    path = oracle_mod.build(out=str(tmp_path / ("mut%d.so" % mutation)),
-                            defines=["ORACLE_MUTATION=%d" % mutation])
-    caught = []
-    # pin A: one gate against dense matrices
+def _pin_phase(oracle_mod, path):
+    """sigma_a sigma_b = i^B sigma_{a xor b} on one site."""
+    for a in "XYZ":
+        for b in "XYZ":
+            I = oracle_mod.index_from_label(a)
+            J = oracle_mod.index_from_label(b)
+            B = oracle_mod.phase_exponent(I, J, 1, lib_path=path)
+            K = tuple(x ^ y for x, y in zip(I, J))
+            lab = "IXYZ"[oracle_mod.codes_from_index(K, 1)[0]]
+            if not np.allclose(bf.PAULI[a] @ bf.PAULI[b], (1j ** B) * bf.PAULI[lab]):
+                return False
+    return True
+
+
+def _pin_dense(oracle_mod, path):
+    """One gate against dense matrices, generic and Clifford angles."""
     rng = random.Random(7)
-    for trial in range(20):
+    for trial in range(24):
         terms = [(random_label(rng, 2), rng.uniform(-1, 1)) for _ in range(3)]
         J = random_label(rng, 2, allow_identity=False)
-        got, ref = _single_gate_case(oracle_mod, 2, terms, J, 0.3 + trial, path)
+        theta = [0.3 + trial, math.pi / 2, -math.pi / 2, math.pi][trial % 4]
+        got, ref = _single_gate_case(oracle_mod, 2, terms, J, theta, path)
         try:
             _assert_same_pauli_sum(got, ref)
         except AssertionError:
-            caught.append("dense")
-            break
-    # pin B: the 12-qubit chain against the state vector
+            return False
+    return True
+
+
+def _pin_statevector(oracle_mod, path):
+    """The 12-qubit chain against the state vector."""
     n = 12
     layers = W.kicked_ising_layers(n, W.chain_edges(n), math.pi / 4)
     m, _ = oracle_mod.run_layers(n, [(W.z_label(n, [6]), 1.0)], layers, 3, 0.0, lib_path=path)
-    if np.max(np.abs(np.array(m) - np.array(bf.statevector_magnetization(n, layers, 3, 6)))) > 1e-12:
-        caught.append("statevector")
-    # pin C: Clifford point theta = pi/2 keeps one string
+    return np.max(np.abs(np.array(m) - np.array(bf.statevector_magnetization(n, layers, 3, 6)))) <= 1e-12
+
+
+def _pin_clifford(oracle_mod, path):
+    """theta = pi/2 on the heavy hex keeps one string."""
     nh, edges = W.heavy_hex_eagle()
     _, op = oracle_mod.run_layers(nh, [(W.z_label(nh, [62]), 1.0)],
                                   W.kicked_ising_layers(nh, edges, math.pi / 2), 3, 0.0,
                                   lib_path=path)
-    if len(op) != 1:
-        caught.append("clifford")
-    assert caught, "mutation %d escaped every pin" % mutation
+    return len(op) == 1
+
+
+def _pin_table_relative(oracle_mod, path):
+    """The Table's eps0 = 1e-5 column (relative truncation), t = 1..5."""
+    nh, edges = W.heavy_hex_eagle()
+    layers = W.kicked_ising_layers(nh, edges, 0.9 * math.pi)
+    m, _ = oracle_mod.run_layers(nh, [(W.z_label(nh, [62]), 1.0)], layers, 5, 1e-5, mode="rel",
+                                 lib_path=path)
+    return all(abs(got - e5) < 1e-13 for (_, _, _, e5), got in zip(_table(), m))
+
+
+def _pin_relative_hand(oracle_mod, path):
+    """The hand examples of the relative rule."""
+    try:
+        a, b, _ = _relative_hand_cases(oracle_mod, path)
+    except Exception:
+        return False
+    return "X" in a and b == {"Z": 1.0}
+
+
+# Cheapest first: a mistake that blows the operator up is caught by the
+# small pins before the heavy-hex runs meet it.
+PINS = [("phase", _pin_phase), ("dense", _pin_dense), ("relative_hand", _pin_relative_hand),
+        ("statevector", _pin_statevector), ("clifford", _pin_clifford),
+        ("table_relative", _pin_table_relative)]
+
+
+def _first_failing_pin(oracle_mod, path):
+    """The pins above, re-run in order on the oracle built at ``path``; the
+    name of the first that fails, or None."""
+    for name, pin in PINS:
+        if not pin(oracle_mod, path):
+            return name
+    return None
+
+
+# Each planted mistake (see the list at the top of orqa_oracle.cpp) and the
+# first pin, in the order above, that catches it.
+MUTATIONS = {
+    1: "dense",            # Algorithm 1's source-indexed sign
+    2: "dense",            # sin term taken from the updated value
+    3: "clifford",         # no exact Clifford angles: ghost strings
+    4: "statevector",      # sigma_y counted as diagonal in <0|O|0>
+    5: "clifford",         # exact zeros kept
+    6: "phase",            # Levi-Civita orientation reversed
+    7: "dense",            # commuting strings rotated too
+    8: "relative_hand",    # relative threshold from the max before the gate
+    9: "dense",            # a branch overwrites the term already at its destination
+    10: "dense",           # sin sign reversed at the Clifford angles
+}
+
+
+def test_default_oracle_passes_every_pin(oracle_mod):
+    assert _first_failing_pin(oracle_mod, oracle_mod.build()) is None
+
+
+@pytest.mark.parametrize("mutation", sorted(MUTATIONS))
+def test_planted_mistakes_are_caught(oracle_mod, tmp_path, mutation):
+    path = oracle_mod.build(out=str(tmp_path / ("mut%d.so" % mutation)),
+                            defines=["ORACLE_MUTATION=%d" % mutation])
+    assert _first_failing_pin(oracle_mod, path) == MUTATIONS[mutation]
 
 
 def test_histogram_hand_example(oracle_mod):
