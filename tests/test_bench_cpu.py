@@ -50,3 +50,36 @@ def test_error_entry_and_names():
     assert cfg["coefficients"] == "fp32" and cfg["n_qubits"] == 127 and "l2" in cfg
     host = bench.host_cpu()
     assert host["nproc"] >= 1 and host["model"]
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True,
+                         text=True, env=env, cwd=ROOT, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm times the CPU oracle on the arm's own metric and
+    workload; one JSON line, no GPU needed."""
+    lines = _run_bench(["--impl", "reference", "--steps", "2", "--warmup", "1", "--workload", "chain12"])
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "chain12"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs and prints the reference line."""
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", "chain12"],
+                      {"RANK": "1", "WORLD_SIZE": "2"}) == []
