@@ -666,7 +666,7 @@ def main(argv=None):
         # The precision form's error per step against the GPU FP64 path on
         # the same workload (one untimed evolution after the timed run).
         line["magnetization_error_vs_gpu_fp64"] = error_entry(res["mags"], fp64_magnetization(wl, res["capacity"]))
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline is an N = 1 figure
         cb = cpu_baseline(wl, args.cpu_seconds)
         om = cb.pop("magnetization")
         line["magnetization_error_vs_oracle"] = error_entry(res["mags"], om)
