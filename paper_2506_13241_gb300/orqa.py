@@ -161,6 +161,8 @@ def strings_from_labels(labels, n_qubits: int):
     x = np.zeros((len(labels), W), dtype=np.uint64)
     z = np.zeros((len(labels), W), dtype=np.uint64)
     for i, lab in enumerate(labels):
+        if len(lab) > n_qubits or set(lab) - set("IXYZ"):
+            raise ValueError("label %r: at most %d characters from I, X, Y, Z" % (lab, n_qubits))
         for q, ch in enumerate(lab):
             bit = np.uint64(1) << np.uint64(q % 64)
             if ch in "XY":

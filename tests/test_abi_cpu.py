@@ -94,6 +94,15 @@ def test_label_encoding_matches_paper_codes():
     assert list(codes[0][:4]) == [0, 1, 2, 3]
 
 
+def test_bad_labels_are_rejected():
+    import pytest
+    for bad in (["IXQZ"], ["x"], ["I" * 13]):
+        with pytest.raises(ValueError):
+            orqa.strings_from_labels(bad, 12)
+    x, z = orqa.strings_from_labels(["", "I" * 12], 12)
+    assert not x.any() and not z.any()
+
+
 def test_null_context_is_rejected_before_any_cuda_call(lib):
     """Every entry point that takes a context returns ORQA_EINVAL for a null
     one, without touching CUDA."""
