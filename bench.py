@@ -450,6 +450,21 @@ def sweep_from_name(name: str):
     return wl
 
 
+def shard_sweep(wl, rank, world):
+    """The problems of one rank when N ranks share a sweep: problem p goes to
+    rank p mod N.  The problems are independent, so the ranks exchange no
+    data; round-robin gives every rank a similar mix of angles and
+    observable weights.  One rank: the sweep itself."""
+    if world <= 1:
+        return wl
+    idx = list(range(rank, len(wl["problems"]), world))
+    out = dict(wl)
+    out["problems"] = [wl["problems"][p] for p in idx]
+    out["theta"] = [wl["theta"][p] for p in idx]
+    out["problem_index"] = idx
+    return out
+
+
 def sweep_inputs(wl):
     import numpy as np
     from paper_2506_13241_gb300 import orqa as B
@@ -577,22 +592,41 @@ def run_sweep(args, wl, rank, world):
 
 
 def main_sweep(args, world, rank):
+    """The batched sweep.  On N ranks its problems are sharded (problem p on
+    rank p mod N, no data exchanged): the total work is fixed, so the
+    scaling is strong; the time is the slowest rank's and the updates are
+    summed over the ranks."""
     import numpy as np
     if world > 1:
-        raise SystemExit("sweep workloads run on one GPU (one batched context)")
-    wl = sweep_from_name(args.workload)
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    wl_all = sweep_from_name(args.workload)
+    wl = shard_sweep(wl_all, rank, world)
     from paper_2506_13241_gb300 import build
     if rank == 0:
         build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     res = run_sweep(args, wl, rank, world)
-    secs = res["total_ms"] * 1e-3
-    value = res["updates"] * world / secs
-    P = len(wl["problems"])
+    times, sums = reduce_over_ranks([res["total_ms"], res["e2e_s"]], [res["updates"], res["e2e_updates"]], "cuda")
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    total_ms, e2e_s = times
+    updates, e2e_updates = sums
+    secs = total_ms * 1e-3
+    value = updates / secs
+    P = len(wl_all["problems"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": wl["name"], "lattice": "heavy-hex 127", "problems": P,
+            "config": {"workload": wl_all["name"], "lattice": "heavy-hex 127", "problems": P,
                        "theta_x": "%d values uniform in [0, pi/2]" % (P // len(wl["weights"])),
                        "observables": "Z-strings of weight %s around qubit 62" % wl["weights"],
                        "time_steps": wl["steps"], "delta": wl["delta"],
@@ -600,14 +634,16 @@ def main_sweep(args, world, rank):
                        "coefficients": args.precision, "execution": "one captured CUDA graph per step",
                        "l2": "flushed between timed steps"},
             "roofline": roofline_entry(res["prof"], 1),
-            "e2e": {"value": res["e2e_updates"] * world / res["e2e_s"], "unit": UNIT,
+            "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "peak_strings": res["stats"]["last_layer_peak"], "chunk_passes_per_step": res["stats"]["chunk_passes"],
             "final_sizes": {"total": int(res["sizes"].sum()), "max": int(res["sizes"].max())}}
+    if world > 1:
+        line["config"]["sharding"] = "problem p on rank p mod %d; no data exchanged" % world
     if res["tuned"]:
         line["autotune"] = res["tuned"]
-    if args.compare_plain:
+    if args.compare_plain and world == 1:
         plain, pm = run_plain_sweep(wl, int(6e7))
         line["plain_fp64_sequential"] = plain
         line["speedup_vs_plain_fp64"] = value / plain["value"]
@@ -615,6 +651,9 @@ def main_sweep(args, world, rank):
         line["magnetization_error_vs_plain_fp64"] = {"max_abs": float(diff.max()),
                                                      "per_step_max": [float(v) for v in diff.max(axis=1)]}
     print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def main(argv=None):

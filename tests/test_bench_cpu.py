@@ -83,3 +83,21 @@ def test_reference_arm_other_ranks_exit_quietly():
     """Under torchrun only rank 0 runs and prints the reference line."""
     assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", "chain12"],
                       {"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_sweep_shards_partition_the_problems():
+    """On N ranks the sweep's problems are split round-robin: every problem
+    on exactly one rank, shard sizes within one, angles kept with their
+    problems."""
+    wl = bench.sweep_from_name("sweep_n=5_t=2_delta=1e-3")
+    P = len(wl["problems"])
+    assert bench.shard_sweep(wl, 0, 1) is wl
+    for world in (2, 3, 4, 7):
+        shards = [bench.shard_sweep(wl, r, world) for r in range(world)]
+        seen = sorted(p for sh in shards for p in sh["problem_index"])
+        assert seen == list(range(P))
+        sizes = [len(sh["problems"]) for sh in shards]
+        assert max(sizes) - min(sizes) <= 1
+        for sh in shards:
+            for k, p in enumerate(sh["problem_index"]):
+                assert sh["problems"][k] == wl["problems"][p] and sh["theta"][k] == wl["theta"][p]
