@@ -318,7 +318,10 @@ orqa_status orqa_set_tuning(orqa_ctx* ctx, const orqa_tuning* in);
  * operator (restored before every run) and timed with CUDA events around
  * the graph launch, and the fastest value is kept.  The best tuning is left
  * set, *best_ms (may be NULL) receives its time, and the operator is
- * restored.  The operator must fit the host memory of one export. */
+ * restored.  If a run fails (for example a capacity overflow under one of
+ * the candidate settings), the call returns that run's status and message
+ * with the starting tuning and the starting operator put back.  The
+ * operator must fit the host memory of one export. */
 orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t n_layers,
                           int32_t repeat, double delta, int32_t trials, orqa_tuning* best,
                           double* best_ms);

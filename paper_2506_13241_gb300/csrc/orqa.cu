@@ -1711,8 +1711,18 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
     };
     orqa_tuning cur_t;
     orqa_get_tuning(ctx, &cur_t);
+    const orqa_tuning start_t = cur_t;
+    // a failed run leaves the starting tuning and operator in place, and the
+    // message of the failure
+    auto give_up = [&](orqa_status s) -> orqa_status {
+        const std::string msg = ctx->err;
+        orqa_set_tuning(ctx, &start_t);
+        restore();
+        ctx->err = msg;
+        return s;
+    };
     double cur_ms = 0.0;
-    if ((st = measure(cur_t, &cur_ms)) != ORQA_OK) return st;
+    if ((st = measure(cur_t, &cur_ms)) != ORQA_OK) return give_up(st);
     const int targets[] = {192, 256, 320, 448, 640};
     const int subs[] = {384, 512};
     const int densities[] = {8, 16, 32};
@@ -1728,7 +1738,7 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
             field = vals[i];
             if (fine_buckets(ctx->cap, t.bucket_density) > ctx->n_fine_max) continue;
             double ms = 0.0;
-            if ((st = measure(t, &ms)) != ORQA_OK) return st;
+            if ((st = measure(t, &ms)) != ORQA_OK) return give_up(st);
             if (ms < cur_ms) {
                 cur_ms = ms;
                 cur_t = t;
