@@ -23,8 +23,10 @@ from paper_2506_13241_gb300 import workloads as W
 CHUNK = 5
 
 
-def _chunk_pass_layer(strings, gates, delta, cos_sin):
-    """strings: {(x, z): c}; gates: [(q, theta)] on ascending qubits."""
+def _chunk_pass_layer(strings, gates, delta, cos_sin, planted=False):
+    """strings: {(x, z): c}; gates: [(q, theta)] on ascending qubits.
+    planted: the sin terms of a two-member pair enter with swapped signs
+    (the source-indexed sign of Algorithm 1 as printed)."""
     M = 0
     rot = {}
     for q, theta in gates:
@@ -62,7 +64,9 @@ def _chunk_pass_layer(strings, gates, delta, cos_sin):
                 new = {}
                 for l in sorted({s & ~bit for s in slots}):
                     a, b = slots.get(l), slots.get(l | bit)   # sigma_z at q, sigma_y at q
-                    if a is not None and b is not None:
+                    if a is not None and b is not None and planted:
+                        na, nb = co * a + si * b, co * b - si * a
+                    elif a is not None and b is not None:
                         na, nb = co * a - si * b, co * b + si * a
                     elif a is not None:
                         na, nb = co * a, si * a
@@ -98,7 +102,7 @@ def _as_planes(oracle_mod, op, n):
     return {_planes(oracle_mod, k, n): c for k, c in op.as_dict().items()}
 
 
-def _run(oracle_mod, n, terms, layers, delta):
+def _run(oracle_mod, n, terms, layers, delta, planted=False):
     """Applies the layers to the oracle (gate by gate) and to the model (ZZ
     layers through the oracle, X layers by chunk passes); compares after
     every X layer."""
@@ -111,7 +115,8 @@ def _run(oracle_mod, n, terms, layers, delta):
             op.apply(g, delta)
         if layer[0][0] != "rx":
             continue
-        got = _chunk_pass_layer(before, [(g[1], g[3]) for g in layer], delta, oracle_mod.rotation_cos_sin)
+        got = _chunk_pass_layer(before, [(g[1], g[3]) for g in layer], delta, oracle_mod.rotation_cos_sin,
+                                planted)
         assert got == _as_planes(oracle_mod, op, n)
     return len(op)
 
@@ -152,3 +157,11 @@ def test_small_strings_entering_a_layer(oracle_mod):
              ("IZIIII", 1e-5), ("IZIZII", 0.9), ("IYIIZI", -0.3)]
     layer = [("rx", q, None, th) for q, th in ((1, 0.4), (3, -1.1), (4, math.pi / 4))]
     assert _run(oracle_mod, n, terms, [layer, layer], 1e-3) > 4
+
+
+def test_planted_sign_is_caught(oracle_mod):
+    """The same comparison sees the two-member update with swapped signs."""
+    n, edges = W.heavy_hex_eagle()
+    layers = W.kicked_ising_layers(n, edges, math.pi / 4)
+    with pytest.raises(AssertionError):
+        _run(oracle_mod, n, [(W.z_label(n, [62]), 1.0)], layers * 4, 1e-4, planted=True)

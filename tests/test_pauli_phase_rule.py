@@ -32,12 +32,15 @@ def _planes(codes):
     return x, z
 
 
-def _kernel_rule(jx_, jz_, x, z, n):
-    """(anticommutes, child factor) by the kernel's plane arithmetic."""
+def _kernel_rule(jx_, jz_, x, z, n, planted=False):
+    """(anticommutes, child factor) by the kernel's plane arithmetic.
+    planted: B counted as B(P, J) instead of B(J, P) (operands swapped)."""
     full = (1 << n) - 1
     anti = bin((x & jz_) ^ (z & jx_)).count("1") & 1
     jx, jy, jz = jx_ & ~jz_ & full, jx_ & jz_, ~jx_ & jz_ & full
     px, py, pz = x & ~z & full, x & z, ~x & z & full
+    if planted:
+        (jx, jy, jz), (px, py, pz) = (px, py, pz), (jx, jy, jz)
     plus = bin((jx & py) | (jy & pz) | (jz & px)).count("1")
     minus = bin((jx & pz) | (jy & px) | (jz & py)).count("1")
     B = (plus - minus) & 3
@@ -63,3 +66,22 @@ def test_plane_rule_matches_oracle(oracle_mod, n):
             assert got == {(x, z): 1.0}, trial
         else:
             assert got == {(x, z): c, (x ^ jx, z ^ jz): factor * s}, trial
+
+
+def test_planted_operand_order_is_caught(oracle_mod):
+    """The same comparison sees B(P, J) used in place of B(J, P)."""
+    rng = random.Random(3)
+    n, theta = 4, 0.7
+    c, s = oracle_mod.rotation_cos_sin(theta)
+    caught = 0
+    for _ in range(60):
+        x, z, jx, jz = (rng.getrandbits(n) for _ in range(4))
+        anti, factor = _kernel_rule(jx, jz, x, z, n, planted=True)
+        if not anti:
+            continue
+        op = oracle_mod.Oracle(n)
+        op.add_label(_label(x, z, n), 1.0)
+        op.rotate_only(("pauli", oracle_mod.index_from_label(_label(jx, jz, n)), None, theta))
+        got = {_planes(oracle_mod.codes_from_index(k, n)): v for k, v in op.as_dict().items()}
+        caught += got.get((x ^ jx, z ^ jz)) != factor * s
+    assert caught > 0
