@@ -132,11 +132,12 @@ def test_relative_truncation_random(orqa, oracle_mod):
 
 @pytest.mark.parametrize("delta", [1e-4, 1e-5])
 def test_fp32_precision_form(orqa, oracle_mod, delta):
-    """ORQA_FLAG_FP32 (BASELINE config 4): coefficients in FP32, two-member
-    pair updates by the compensated Dot2 scheme, FP64 expectation sum.  The
-    magnetization must stay within 1e-6 of the FP64 oracle: each coefficient
-    sees a few hundred FP32 roundings (2^-24 relative) through 5 steps, and
-    cos, sin themselves are rounded to FP32 (1.2e-8 at theta = pi/4)."""
+    """ORQA_FLAG_FP32 on the 127-qubit heavy hex (Z_62, theta = pi/4, 5
+    steps): coefficients in FP32, two-member pair updates by the compensated
+    Dot2 scheme, cos and sin as float pairs hi + lo, FP64 expectation sum.
+    The magnetization must stay within 1e-6 of the FP64 oracle: each
+    coefficient sees a few hundred FP32 roundings (2^-24 relative) through
+    5 steps."""
     n, edges = W.heavy_hex_eagle()
     layers = W.kicked_ising_layers(n, edges, math.pi / 4)
     ctx = orqa.Context(n, 1 << 23, fp32=True)
