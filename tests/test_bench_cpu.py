@@ -101,3 +101,26 @@ def test_sweep_shards_partition_the_problems():
         for sh in shards:
             for k, p in enumerate(sh["problem_index"]):
                 assert sh["problems"][k] == wl["problems"][p] and sh["theta"][k] == wl["theta"][p]
+
+
+def test_clock_summary_from_nvidia_smi_lines():
+    """The clocks entry: median SM clock under load, the maximum clock, and
+    every throttle reason seen Active (nvidia-smi csv, noheader, nounits)."""
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    cs = bench.ClockSampler(0)
+    cs.proc = _Done()
+    cs.lines = [
+        "2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1980, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "",
+    ]
+    assert cs.stop() == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
