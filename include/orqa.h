@@ -182,8 +182,9 @@ orqa_status orqa_apply_pauli_rotation(orqa_ctx* ctx, const uint64_t* xj, const u
                                       double theta, double delta, int64_t* n_live_out);
 
 /* Merges duplicate strings (sums their coefficients) and drops c == 0 and
- * |c| < delta: the insert-or-add and truncate loops of Algorithm 1 applied
- * to the whole operator.  n_live_out (may be NULL) receives |O|. */
+ * |c| < delta (with ORQA_FLAG_RELATIVE: |c| <= delta * max|c|, the max over
+ * the merged operator): the insert-or-add and truncate loops of Algorithm 1
+ * applied to the whole operator.  n_live_out (may be NULL) receives |O|. */
 orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out);
 
 /* <0|O|0> = sum of O_I over strings with no sigma_x / sigma_y factor
