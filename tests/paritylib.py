@@ -60,5 +60,3 @@ def assert_bit_exact(gpu, ora, what=""):
             what, bad.size, bad[0], gv[bad[0]], ov[bad[0]])
 
 
-def codes_to_labels(codes: np.ndarray):
-    return ["".join("IXYZ"[a] for a in row) for row in codes]
