@@ -175,8 +175,11 @@ def strings_from_labels(labels, n_qubits: int):
 def gate_array(gates):
     """orqa_gate[] from workload tuples (kind, q0, q1, theta)."""
     arr = (orqa_gate * len(gates))()
+    kinds = {"rx": ORQA_RX, "rzz": ORQA_RZZ}
     for k, (kind, q0, q1, theta) in enumerate(gates):
-        arr[k].kind = {"rx": ORQA_RX, "rzz": ORQA_RZZ}[kind]
+        if kind not in kinds:
+            raise ValueError("gate %d: kind %r is not one of %s" % (k, kind, sorted(kinds)))
+        arr[k].kind = kinds[kind]
         arr[k].q0 = int(q0)
         arr[k].q1 = int(q1) if q1 is not None else 0
         arr[k].pad = 0

@@ -94,6 +94,18 @@ def test_label_encoding_matches_paper_codes():
     assert list(codes[0][:4]) == [0, 1, 2, 3]
 
 
+def test_bad_gates_and_programs_are_rejected():
+    import numpy as np
+    import pytest
+    with pytest.raises(ValueError):
+        orqa.gate_array([("ry", 0, None, 0.1)])
+    xx = [("rx", q, None, 0.3) for q in range(4)]
+    with pytest.raises(ValueError):
+        orqa.Program([(xx, True, np.zeros((2, 3)))], n_problems=2)   # theta must be [P, n_gates]
+    prog = orqa.Program([(xx, True, np.zeros((2, 4))), (xx, False, None)], n_problems=2)
+    assert prog.n_expect_per_rep == 1 and prog.desc[0].n_gates == 4 and prog.desc[1].theta is None
+
+
 def test_bad_labels_are_rejected():
     import pytest
     for bad in (["IXQZ"], ["x"], ["I" * 13]):
