@@ -115,6 +115,15 @@ typedef struct {
     int64_t pair_updates_two; /* (pair, gate) updates with both members present */
     int32_t chunk_passes;     /* device passes its rotation layer took */
     int32_t pad;
+    double sum_sq;            /* sum of c^2 over the live strings (FP64, fixed summation
+                                 order): 1 for a normalised Pauli-string observable, kept by
+                                 every rotation (Eq. update_rule is an orthogonal 2x2 map on
+                                 each pair) and lowered only by truncation */
+    double max_abs;           /* max |c| over the live strings (exact) */
+    double dropped_sum_sq;    /* sum of c^2 of the strings the last call's truncation
+                                 removed (Eq. truncation1), so that sum_sq before minus
+                                 sum_sq after equals it up to rounding; NaN for a call whose
+                                 X layers ran without orqa_set_norm_tracking */
 } orqa_stats_t;
 
 /* Per-kernel launch profile (ORQA_FLAG_PROFILE).  bytes is the kernel's
@@ -192,8 +201,12 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
 orqa_status orqa_expect(orqa_ctx* ctx, double* out);
 
 /* Copies the operator to HOST arrays (cap strings at most; x, z: cap*W
- * words, c: cap doubles) in an unspecified order; *n_out receives |O|.
- * ECAPACITY (nothing copied) if |O| > cap. */
+ * words, c: cap doubles) in canonical order: ascending by the 256-bit key
+ * of the string, x words from the highest to the lowest, then z words
+ * likewise (batched contexts: by problem index first).  The order is made
+ * on the device (a radix sort in the context's free buffers; the operator
+ * is not modified).  *n_out receives |O|.  ECAPACITY (nothing copied) if
+ * |O| > cap. */
 orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c,
                         int64_t* n_out);
 
@@ -210,8 +223,21 @@ orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, do
 orqa_status orqa_histogram(orqa_ctx* ctx, int32_t n_bins, double log10_lo, int64_t* counts,
                            double* max_abs_out);
 
-/* Counters of the operator and of the last apply_layer call. */
+/* Counters of the operator (|O|, sum c^2, max |c|) and of the last
+ * apply_layer, apply_pauli_rotation, merge_truncate or run_program call
+ * (updates, branch events, dropped strings and their sum of c^2).  The
+ * first call after the operator changed reduces its coefficients on the
+ * device (8 bytes per string) and waits for the stream; later calls return
+ * the cached values. */
 orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out);
+
+/* on = 1: the X-layer kernels also add up the c^2 of every string their
+ * truncation removes (orqa_stats_t.dropped_sum_sq), the bookkeeping that
+ * checks sum_sq_before - sum_sq_after = dropped_sum_sq layer by layer.  It
+ * costs FP64 work in the hot kernels, so it is off (0) by default; no
+ * result changes with it.  Other truncations (ZZ layers, merges, relative
+ * truncation) always report it. */
+orqa_status orqa_set_norm_tracking(orqa_ctx* ctx, int32_t on);
 
 /* Profile of kernel kind `index` (0 <= index < orqa_profile_count()) since
  * the last reset; zeros unless the context was created with
@@ -261,7 +287,8 @@ orqa_status orqa_expect_batch(orqa_ctx* ctx, double* out);
 orqa_status orqa_problem_sizes(orqa_ctx* ctx, int64_t* out);
 
 /* orqa_export plus each string's problem index (problem: cap int32, may be
- * NULL; all 0 for a plain context). */
+ * NULL; all 0 for a plain context), in the same canonical order (problem
+ * index, then key). */
 orqa_status orqa_export_batch(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, double* c,
                               int32_t* problem, int64_t* n_out);
 
@@ -327,6 +354,36 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
                           int32_t repeat, double delta, int32_t trials, orqa_tuning* best,
                           double* best_ms);
 
+/* Test hooks of the failure paths (not for production use).  Each makes a
+ * bounded device-side condition fire without faulting or hanging the GPU,
+ * so that tests can check the status it returns and that the operator held
+ * before the failing call is unchanged.  value 0 restores the default.
+ *   ORQA_DEBUG_SPIN_LIMIT         iterations of the merge hash table's
+ *                                 bounded wait, 1..2^22 (default 2^22)
+ *   ORQA_DEBUG_POISON_MERGE_TABLE 1: later merges start with every table slot
+ *                                 marked as being published by another
+ *                                 thread, so each insertion waits until the
+ *                                 spin limit and the call returns
+ *                                 ORQA_ETIMEOUT
+ *   ORQA_DEBUG_MERGE_TABLE_SLOTS  most hash-table slots a merge may use (a
+ *                                 power of two >= 16): more distinct strings
+ *                                 than slots return ORQA_ECAPACITY
+ *   ORQA_DEBUG_PASS_LIMIT         most chunk passes of an X layer, 1..32 (a
+ *                                 layer needing more returns ORQA_ETIMEOUT)
+ *   ORQA_DEBUG_BUCKET_SHIFT       fine bucket = hash >> shift, from the
+ *                                 default up to 63 (fewer, fuller buckets:
+ *                                 one above the shared-memory range size
+ *                                 returns ORQA_ECAPACITY); orqa_set_tuning
+ *                                 restores the default */
+enum {
+    ORQA_DEBUG_SPIN_LIMIT = 1,
+    ORQA_DEBUG_POISON_MERGE_TABLE = 2,
+    ORQA_DEBUG_MERGE_TABLE_SLOTS = 3,
+    ORQA_DEBUG_PASS_LIMIT = 4,
+    ORQA_DEBUG_BUCKET_SHIFT = 5
+};
+orqa_status orqa_debug_set(orqa_ctx* ctx, int32_t knob, int64_t value);
+
 /* Largest operator orqa_expect_noalloc accepts (2^27 strings). */
 #define ORQA_NOALLOC_MAX_STRINGS 134217728LL
 
@@ -337,15 +394,18 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
  * device memory pool, and latency-critical paths that cannot accept the
  * device-wide synchronisation an allocation may imply.
  *   x: n*W words (string-major, as in orqa_set_operator), c: n doubles, both
- *      on the current device; out: HOST pointer receiving the sum of c over
- *      strings whose x plane is zero, in FP64.  Waits for `stream`.
+ *      device (or managed) memory of the current device, 8-byte aligned;
+ *      out: HOST pointer receiving the sum of c over strings whose x plane is
+ *      zero, in FP64.
+ * The call waits for `stream` (it copies the result to the host), so it
+ * cannot be used inside stream capture.
  * Scratch is a fixed file-scope device array (65537 doubles) that every GPU
- * loading the library holds until exit.  The first call on a device looks up
- * that array's device address, so it should come before any stream capture.
- * All calls share the array: calls whose kernels overlap on the GPU race and
- * must be serialised by the caller.
+ * loading the library holds until exit; the first call on a device looks up
+ * that array's device address.  All calls share the array: calls whose
+ * kernels overlap on the GPU race and must be serialised by the caller.
  * Returns ORQA_ECAPACITY (nothing launched) if n > ORQA_NOALLOC_MAX_STRINGS,
- * ORQA_EINVAL for bad arguments, ORQA_ECUDA if a CUDA call fails. */
+ * ORQA_EINVAL for bad arguments (including host or misaligned pointers,
+ * checked before any launch), ORQA_ECUDA if a CUDA call fails. */
 orqa_status orqa_expect_noalloc(int32_t n_qubits, int64_t n, const uint64_t* x, const double* c,
                                 double* out, void* stream);
 

@@ -14,6 +14,7 @@
 #include "orqa.h"
 #include "orqa_kernels.cuh"
 #include "orqa_layer.cuh"
+#include "orqa_sort.cuh"
 
 using namespace orqa;
 
@@ -86,6 +87,7 @@ struct orqa_ctx {
     uint64_t* hash_active = nullptr;   // unit-key hashes of the active list
     int32_t* rank_active = nullptr;    // ranks inside their fine buckets
     void* records = nullptr;           // bucket-ordered copy of the active list
+    size_t shared_bytes = 0;           // size of the layer / merge scratch region
     size_t local_smem = 0;
     Counters* ctr = nullptr;
     unsigned long long* pop_delta = nullptr;
@@ -103,6 +105,15 @@ struct orqa_ctx {
 
     orqa_stats_t stats{};
     std::string err;
+    // norms of the committed operator (orqa_stats), valid until it changes
+    bool norms_valid = false;
+    double norm_sq = 0.0, norm_max = 0.0;
+    bool track_norm = false;   // orqa_set_norm_tracking
+    // failure-path test hooks (orqa_debug_set)
+    long long spin_limit = SPIN_LIMIT;
+    bool poison_table = false;
+    long long dbg_table_slots = 0;
+    int pass_limit = MAX_PASSES;
 
     // ORQA_FLAG_PROFILE: CUDA events around every launch, resolved at the
     // next stream synchronisation.
@@ -390,6 +401,7 @@ orqa_status reset_counters(orqa_ctx* ctx) {
 orqa_status host_commit(orqa_ctx* ctx, int cur, long long n) {
     ctx->cur = cur;
     ctx->n = n;
+    ctx->norms_valid = false;
     k_set_live<<<1, 32, 0, ctx->stream>>>(ctx->ctr, n, cur);
     LAUNCH_CHECK(ctx);
     return ORQA_OK;
@@ -421,16 +433,22 @@ constexpr double string_bytes() {
 template <int W, typename Tin, typename Tout>
 orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, double delta,
                        long long* n_out) {
-    const long long tcap = std::min(pow2_at_least(2 * (n > 0 ? n : 1)), ctx->table_cap);
+    long long tcap = std::min(pow2_at_least(2 * (n > 0 ? n : 1)), ctx->table_cap);
     if (4 * n > 3 * tcap) return fail(ctx, ORQA_ECAPACITY, "merge: hash table too small");
+    if (ctx->dbg_table_slots > 0) tcap = std::min(tcap, ctx->dbg_table_slots);  // test hook
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     int r_as = -1, r_off = -1, r_sc = -1, r_red = -1;
     if (n > 0) {
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->table, 0xff, (size_t)tcap * 4, ctx->stream));
+        if (ctx->poison_table) {  // test hook: every slot looks busy
+            k_fill_busy<<<grid_for(ctx, tcap), 256, 0, ctx->stream>>>(ctx->table, tcap);
+            LAUNCH_CHECK(ctx);
+        }
         const int g = grid_for(ctx, n);
         r_as = prof_begin(ctx, K_MERGE_ASSIGN, 0);
         k_merge_assign<W><<<g, 256, 0, ctx->stream>>>(src, n, ctx->table, tcap - 1, ctx->unit_z, ctx->unit_xb,
-                                                       ctx->unit_pid, ctx->unit_count, ctx->uid, ctx->rank, ctx->ctr);
+                                                       ctx->unit_pid, ctx->unit_count, ctx->uid, ctx->rank, ctx->ctr,
+                                                       ctx->spin_limit);
         prof_end(ctx, r_as);
         LAUNCH_CHECK(ctx);
         r_off = prof_begin(ctx, K_MERGE_OFFSETS, 0);
@@ -463,6 +481,7 @@ orqa_status merge_into(orqa_ctx* ctx, StrList src, long long n, int dst_buf, dou
     if (st != ORQA_OK) return st;
     *n_out = (long long)h.n_done;
     ctx->stats.dropped = (int64_t)h.dropped;
+    ctx->stats.dropped_sum_sq = h.dropped_sq;
     return ORQA_OK;
 }
 
@@ -529,7 +548,7 @@ orqa_status build_zz_groups(orqa_ctx* ctx, const orqa_gate* g, int ng, std::vect
 // Drops c == 0 and |c| < delta from the committed operator (the truncation
 // loop of Algorithm 1 on its own) into the next buffer.
 template <int W, typename T>
-orqa_status truncate_abs(orqa_ctx* ctx, double delta, long long* dropped) {
+orqa_status truncate_abs(orqa_ctx* ctx, double delta, long long* dropped, double* dropped_sq = nullptr) {
     const int dst = (ctx->cur + 1) % 3;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
     const int r = prof_begin(ctx, K_TRUNCATE, 0);
@@ -544,6 +563,7 @@ orqa_status truncate_abs(orqa_ctx* ctx, double delta, long long* dropped) {
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "truncate")) != ORQA_OK) return st;
     *dropped = ctx->n - (long long)h.n_done;
+    if (dropped_sq) *dropped_sq = h.dropped_sq;
     if ((st = host_commit(ctx, dst, (long long)h.n_done)) != ORQA_OK) return st;
     ctx->clean_delta = delta;
     return ORQA_OK;
@@ -570,11 +590,14 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     ctx->stats.pair_updates_one = 0;
     ctx->stats.pair_updates_two = 0;
     ctx->stats.chunk_passes = 0;
+    ctx->stats.dropped_sum_sq = 0.0;
     if (delta > ctx->clean_delta && ctx->n > 0) {
         long long dropped = 0;
-        orqa_status st = truncate_abs<W, T>(ctx, delta, &dropped);
+        double dsq = 0.0;
+        orqa_status st = truncate_abs<W, T>(ctx, delta, &dropped, &dsq);
         if (st != ORQA_OK) return st;
         ctx->stats.dropped = dropped;
+        ctx->stats.dropped_sum_sq = dsq;
     }
     return ORQA_OK;
 }
@@ -600,6 +623,7 @@ orqa_status build_rx_run(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta
                          RxRun& run) {
     run = RxRun{};
     run.delta = delta;
+    run.track_norm = ctx->track_norm ? 1 : 0;
     run.dbits64 = ge_bits<double>(delta);
     run.dbits32 = (uint32_t)ge_bits<float>(delta);
     run.q_first = g[0].q0;
@@ -689,7 +713,7 @@ orqa_status enqueue_pass(orqa_ctx* ctx, const RxLists& L, const RxRun& run, int 
         L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
     prof_end(ctx, *r_lo);
     LAUNCH_CHECK(ctx);
-    k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 0, cond, use_cond);
+    k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 0, cond, use_cond, ctx->pass_limit);
     LAUNCH_CHECK(ctx);
     return ORQA_OK;
 }
@@ -713,7 +737,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
         prof_end(ctx, r_split);
         LAUNCH_CHECK(ctx);
     }
-    k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 1, 0, 0);
+    k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 1, 0, 0, ctx->pass_limit);
     LAUNCH_CHECK(ctx);
     Counters h{};
     if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
@@ -722,7 +746,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
     int pass = 0;
-    while (h.n_active > 0) {  // ends: k_pass_advance flags an error beyond MAX_PASSES passes
+    while (h.n_active > 0) {  // ends: k_pass_advance flags an error beyond pass_limit passes
         const long long n_active = (long long)h.n_active;
         const unsigned long long done_before = h.n_done;
         int r_sc = -1, r_lo = -1;
@@ -762,6 +786,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     ctx->stats.pair_updates_one = (int64_t)h.pairs_one;
     ctx->stats.pair_updates_two = (int64_t)h.pairs_two;
     ctx->stats.chunk_passes = pass;
+    ctx->stats.dropped_sum_sq = run.track_norm ? h.dropped_sq : std::nan("");
     return ORQA_OK;
 }
 
@@ -769,8 +794,9 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
 // max|c|.  The threshold is eps0 * max formed on the host in FP64, the same
 // product the CPU oracle forms.
 template <int W, typename T>
-orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
+orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped, double* dropped_sq = nullptr) {
     *dropped = 0;
+    if (dropped_sq) *dropped_sq = 0.0;
     if (ctx->n == 0) return ORQA_OK;
     unsigned long long* mx = (unsigned long long*)ctx->scalar;
     CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, 8, ctx->stream));
@@ -796,6 +822,7 @@ orqa_status truncate_relative(orqa_ctx* ctx, double eps0, long long* dropped) {
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "relative truncation")) != ORQA_OK) return st;
     *dropped = ctx->n - (long long)h.n_done;
+    if (dropped_sq) *dropped_sq = h.dropped_sq;
     return host_commit(ctx, dst, (long long)h.n_done);
 }
 
@@ -831,10 +858,12 @@ orqa_status apply_pauli_impl(orqa_ctx* ctx, const uint64_t* xj, const uint64_t* 
     const double dabs = ctx->relative ? 0.0 : delta;
     if ((st = merge_into<W, T, T>(ctx, ctx->buf[stage], (long long)h.n_done, out, dabs, &m)) != ORQA_OK) return st;
     const long long dropped_merge = ctx->stats.dropped;
+    const double dsq_merge = ctx->stats.dropped_sum_sq;
     if ((st = host_commit(ctx, out, m)) != ORQA_OK) return st;
     long long dropped_rel = 0;
+    double dsq_rel = 0.0;
     if (ctx->relative) {
-        if ((st = truncate_relative<W, T>(ctx, delta, &dropped_rel)) != ORQA_OK) return st;
+        if ((st = truncate_relative<W, T>(ctx, delta, &dropped_rel, &dsq_rel)) != ORQA_OK) return st;
         ctx->clean_delta = 0.0;
     } else {
         ctx->clean_delta = delta;
@@ -844,6 +873,7 @@ orqa_status apply_pauli_impl(orqa_ctx* ctx, const uint64_t* xj, const uint64_t* 
     ctx->stats.string_gate_updates = n_in;
     ctx->stats.branch_events = (int64_t)branches;
     ctx->stats.dropped = dropped_merge + dropped_rel;
+    ctx->stats.dropped_sum_sq = dsq_merge + dsq_rel;
     ctx->stats.pair_updates_one = 0;
     ctx->stats.pair_updates_two = 0;
     ctx->stats.chunk_passes = 0;
@@ -898,24 +928,27 @@ template <int W, typename T>
 orqa_status apply_layer_relative(orqa_ctx* ctx, const orqa_gate* g, int ng, double eps0) {
     orqa_stats_t acc{};
     long long dropped = 0;
+    double dsq = 0.0;
     orqa_status st;
     if (g[0].kind == ORQA_RZZ) {
         if ((st = apply_rzz<W, T>(ctx, g, ng, 0.0)) != ORQA_OK) return st;
         acc = ctx->stats;
-        if ((st = truncate_relative<W, T>(ctx, eps0, &dropped)) != ORQA_OK) return st;
+        if ((st = truncate_relative<W, T>(ctx, eps0, &dropped, &dsq)) != ORQA_OK) return st;
         acc.dropped += dropped;
+        acc.dropped_sum_sq += dsq;
     } else {
         for (int k = 0; k < ng; ++k) {
             if (k > 0 && g[k].q0 <= g[k - 1].q0)
                 return fail(ctx, ORQA_EINVAL, "ORQA_RX gates of one layer must have strictly ascending qubits");
             if ((st = apply_rx<W, T>(ctx, &g[k], 1, 0.0, nullptr)) != ORQA_OK) return st;
-            if ((st = truncate_relative<W, T>(ctx, eps0, &dropped)) != ORQA_OK) return st;
+            if ((st = truncate_relative<W, T>(ctx, eps0, &dropped, &dsq)) != ORQA_OK) return st;
             const orqa_stats_t& s = ctx->stats;
             if (k == 0) acc.last_layer_in = s.last_layer_in;
             acc.last_layer_peak = std::max(acc.last_layer_peak, s.last_layer_peak);
             acc.string_gate_updates += s.string_gate_updates;
             acc.branch_events += s.branch_events;
             acc.dropped += s.dropped + dropped;
+            acc.dropped_sum_sq += s.dropped_sum_sq + dsq;
             acc.pair_updates_one += s.pair_updates_one;
             acc.pair_updates_two += s.pair_updates_two;
             acc.chunk_passes += s.chunk_passes;
@@ -956,6 +989,33 @@ orqa_status expect_impl(orqa_ctx* ctx, double* out) {
     CUDA_TRY(ctx, cudaMemcpyAsync(out, dev, (size_t)ctx->P * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     prof_resolve(ctx);
+    return ORQA_OK;
+}
+
+// Sum of c^2 and max |c| of the committed operator (k_norms_partial, then
+// the block partials added in a fixed order), cached until it changes.
+template <int W, typename T>
+orqa_status norms_impl(orqa_ctx* ctx) {
+    double sq = 0.0, mx = 0.0;
+    if (ctx->n > 0) {
+        if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;  // error bits of an earlier failed call
+        unsigned long long* mbits = reinterpret_cast<unsigned long long*>(ctx->scalar) + 1;
+        CUDA_TRY(ctx, cudaMemsetAsync(mbits, 0, 8, ctx->stream));
+        k_norms_partial<T><<<EXPECT_BLOCKS, 256, 0, ctx->stream>>>(reinterpret_cast<const T*>(ctx->buf[ctx->cur].c),
+                                                                    ctx->cap, ctx->ctr, ctx->partials, mbits);
+        k_expect_final<<<1, 32, 0, ctx->stream>>>(ctx->partials, EXPECT_BLOCKS, ctx->scalar + 2, ctx->ctr);
+        LAUNCH_CHECK(ctx);
+        double hv[3] = {0.0, 0.0, 0.0};
+        CUDA_TRY(ctx, cudaMemcpyAsync(hv, ctx->scalar, sizeof hv, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        unsigned long long mb;
+        memcpy(&mb, &hv[1], 8);
+        sq = hv[2];
+        mx = from_mag<T>(mb);
+    }
+    ctx->norm_sq = sq;
+    ctx->norm_max = mx;
+    ctx->norms_valid = true;
     return ORQA_OK;
 }
 
@@ -1005,6 +1065,52 @@ orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t
     ctx->clean_delta = 0.0;
     ctx->stats = orqa_stats_t{};
     ctx->err.clear();
+    return ORQA_OK;
+}
+
+// The committed operator in canonical order (orqa_sort.cuh): *out_buf
+// receives the string buffer holding it, which is the committed buffer
+// itself when no digit varies (at most one string, or one key).
+template <int W, typename T>
+orqa_status sorted_buffer(orqa_ctx* ctx, int* out_buf) {
+    *out_buf = ctx->cur;
+    const long long n = ctx->n;
+    if (n <= 1) return ORQA_OK;
+    const int K = 2 * W + (ctx->P > 1 ? 1 : 0);
+    unsigned long long init[2 * (2 * 2 + 1)];
+    for (int k = 0; k < K; ++k) {
+        init[2 * k] = 0ull;
+        init[2 * k + 1] = ~0ull;
+    }
+    unsigned long long* d_oa = reinterpret_cast<unsigned long long*>(ctx->partials);
+    CUDA_TRY(ctx, cudaMemcpyAsync(d_oa, init, (size_t)2 * K * 8, cudaMemcpyHostToDevice, ctx->stream));
+    k_sort_bits<W><<<grid_for(ctx, n), SORT_THREADS, 0, ctx->stream>>>(ctx->buf[ctx->cur], n, K, d_oa);
+    LAUNCH_CHECK(ctx);
+    unsigned long long oa[2 * (2 * 2 + 1)];
+    CUDA_TRY(ctx, cudaMemcpyAsync(oa, d_oa, (size_t)2 * K * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    // blocks: one chunk each; their digit counts must fit the scratch region
+    long long G = std::min<long long>(4ll * ctx->sm_count, (n + 2047) / 2048);
+    G = std::max(1ll, std::min<long long>(G, (long long)(ctx->shared_bytes / (SORT_DIGITS * 4)) - 1));
+    const long long chunk = (n + G - 1) / G;
+    unsigned* hist = reinterpret_cast<unsigned*>(ctx->records);
+    const int free_bufs[2] = {(ctx->cur + 1) % 3, (ctx->cur + 2) % 3};
+    int src = ctx->cur, nxt = 0;
+    for (int k = 0; k < K; ++k) {
+        const unsigned long long vary = oa[2 * k] ^ oa[2 * k + 1];
+        for (int shift = 0; shift < 64; shift += 8) {
+            if (((vary >> shift) & 255ull) == 0) continue;
+            const int dst = free_bufs[nxt];
+            k_sort_hist<W><<<(int)G, SORT_THREADS, 0, ctx->stream>>>(ctx->buf[src], n, chunk, k, shift, hist, (int)G);
+            k_sort_scan<<<1, 1024, 0, ctx->stream>>>(hist, (int)(SORT_DIGITS * G));
+            k_sort_scatter<W, T><<<(int)G, SORT_THREADS, 0, ctx->stream>>>(ctx->buf[src], ctx->buf[dst], n, chunk, k,
+                                                                            shift, hist, (int)G);
+            LAUNCH_CHECK(ctx);
+            src = dst;
+            nxt ^= 1;
+        }
+    }
+    *out_buf = src;
     return ORQA_OK;
 }
 
@@ -1085,6 +1191,7 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
         ctx->sorted_c = (double*)q; q += align_up(C * 8);
         ctx->table = (int32_t*)q;
         ctx->table_cap = L.table_cap;
+        ctx->shared_bytes = L.shared;
         p += L.shared;
     }
     const size_t F = (size_t)L.n_fine;
@@ -1296,7 +1403,10 @@ orqa_status orqa_export_batch(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t*
     *n_out = ctx->n;
     if (ctx->n > cap) return fail(ctx, ORQA_ECAPACITY, "export: operator larger than cap");
     if (ctx->n > 0 && (!x || !z || !c)) return fail(ctx, ORQA_EINVAL, "export: null array");
-    const StrList s = ctx->buf[ctx->cur];
+    int sb = ctx->cur;
+    const orqa_status sst = ORQA_DISPATCH(ctx, sorted_buffer, ctx, &sb);
+    if (sst != ORQA_OK) return sst;
+    const StrList s = ctx->buf[sb];
     const size_t n = (size_t)ctx->n;
     std::vector<float> cf(ctx->fp32 ? n : 0);
     std::vector<uint16_t> pid16(problem && ctx->P > 1 ? n : 0);
@@ -1323,9 +1433,53 @@ orqa_status orqa_export(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t* z, do
 
 orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out) {
     if (!ctx || !out) return ORQA_EINVAL;
+    if (!ctx->norms_valid) {
+        const orqa_status st = ORQA_DISPATCH(ctx, norms_impl, ctx);
+        if (st != ORQA_OK) return st;
+    }
     ctx->stats.n_strings = ctx->n;
+    ctx->stats.sum_sq = ctx->norm_sq;
+    ctx->stats.max_abs = ctx->norm_max;
     *out = ctx->stats;
     return ORQA_OK;
+}
+
+orqa_status orqa_set_norm_tracking(orqa_ctx* ctx, int32_t on) {
+    if (!ctx || (on != 0 && on != 1)) return ORQA_EINVAL;
+    ctx->track_norm = on != 0;
+    return ORQA_OK;
+}
+
+orqa_status orqa_debug_set(orqa_ctx* ctx, int32_t knob, int64_t value) {
+    if (!ctx) return ORQA_EINVAL;
+    switch (knob) {
+    case ORQA_DEBUG_SPIN_LIMIT:
+        if (value < 0 || value > SPIN_LIMIT) return fail(ctx, ORQA_EINVAL, "debug_set: spin limit out of range");
+        ctx->spin_limit = value ? value : SPIN_LIMIT;
+        return ORQA_OK;
+    case ORQA_DEBUG_POISON_MERGE_TABLE:
+        if (value != 0 && value != 1) return fail(ctx, ORQA_EINVAL, "debug_set: poison is 0 or 1");
+        ctx->poison_table = value != 0;
+        return ORQA_OK;
+    case ORQA_DEBUG_MERGE_TABLE_SLOTS:
+        if (value != 0 && (value < 16 || (value & (value - 1)) != 0 || value > ctx->table_cap))
+            return fail(ctx, ORQA_EINVAL, "debug_set: table slots must be 0 or a power of two in [16, table size]");
+        ctx->dbg_table_slots = value;
+        return ORQA_OK;
+    case ORQA_DEBUG_PASS_LIMIT:
+        if (value < 0 || value > MAX_PASSES) return fail(ctx, ORQA_EINVAL, "debug_set: pass limit out of range");
+        ctx->pass_limit = value ? (int)value : MAX_PASSES;
+        return ORQA_OK;
+    case ORQA_DEBUG_BUCKET_SHIFT: {
+        const int base = 64 - __builtin_ctzll((unsigned long long)ctx->n_fine);
+        if (value != 0 && (value < base || value > 63))
+            return fail(ctx, ORQA_EINVAL, "debug_set: bucket shift must be 0 or in [default, 63]");
+        ctx->fshift = value ? (int)value : base;
+        return ORQA_OK;
+    }
+    default:
+        return fail(ctx, ORQA_EINVAL, "debug_set: unknown knob");
+    }
 }
 
 int32_t orqa_profile_count(void) { return K_COUNT; }
@@ -1428,8 +1582,8 @@ orqa_status prepare_program(orqa_ctx* ctx, const orqa_layer_desc* d, int nl, int
 
 uint64_t program_key(const orqa_ctx* ctx, const orqa_layer_desc* d, int nl, int repeat, double delta) {
     uint64_t h = 0xcbf29ce484222325ull;
-    const int head[9] = {ctx->W, ctx->P, ctx->fp32 ? 1 : 0, ctx->cur, repeat, ctx->range_target, ctx->sub_max,
-                         ctx->n_fine, ctx->grid_per_sm};
+    const int head[12] = {ctx->W, ctx->P, ctx->fp32 ? 1 : 0, ctx->cur, repeat, ctx->range_target, ctx->sub_max,
+                          ctx->n_fine, ctx->grid_per_sm, ctx->fshift, ctx->pass_limit, ctx->track_norm ? 1 : 0};
     h = fnv(h, head, sizeof head);
     h = fnv(h, &delta, sizeof delta);
     for (int l = 0; l < nl; ++l) {
@@ -1483,7 +1637,7 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
                 CAPTURE_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
                 cudaGraphConditionalHandle h;
                 CAPTURE_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-                k_pass_advance<<<1, 32, 0, cs>>>(ctx->ctr, 1, h, 1);
+                k_pass_advance<<<1, 32, 0, cs>>>(ctx->ctr, 1, h, 1, ctx->pass_limit);
                 CAPTURE_TRY(cudaGetLastError());
                 const cudaGraphNode_t* deps = nullptr;
                 size_t nd = 0;
@@ -1611,6 +1765,7 @@ orqa_status run_program_impl(orqa_ctx* ctx, const orqa_layer_desc* d, int nl, in
     // the committed operator (after the last completed layer)
     ctx->cur = h.cur;
     ctx->n = (long long)h.n_live;
+    ctx->norms_valid = false;
     bool any_x = false;
     for (const ProgLayer& L : pl) any_x = any_x || L.kind == ORQA_RX;
     if (any_x && ps.x_layers > 0) ctx->clean_delta = delta;
@@ -1622,6 +1777,7 @@ orqa_status run_program_impl(orqa_ctx* ctx, const orqa_layer_desc* d, int nl, in
     ctx->stats.pair_updates_one = (int64_t)ps.pairs_one;
     ctx->stats.pair_updates_two = (int64_t)ps.pairs_two;
     ctx->stats.chunk_passes = (int32_t)ps.passes;
+    ctx->stats.dropped_sum_sq = ctx->track_norm ? ps.dropped_sq : std::nan("");
     ctx->stats.n_strings = ctx->n;
     if (h.err) {
         char where[96];

@@ -13,7 +13,7 @@ constexpr int MAX_QUBITS = 128;
 constexpr int CHUNK_BITS = 5;     // rotation qubits per unit pass: 2^5 = one warp
 constexpr int32_t SLOT_EMPTY = -1;
 constexpr int32_t SLOT_BUSY = -2;
-constexpr long long SPIN_LIMIT = 1LL << 22;
+constexpr long long SPIN_LIMIT = 1LL << 22;   // default bound of every spin-wait
 
 // String list in structure-of-arrays form.  x and z are string-major
 // (word w of string i at x[i*W + w]) so that W = 2 loads as one 16-byte
@@ -55,6 +55,7 @@ struct Counters {
     unsigned long long split_dropped;  // strings the entry split dropped
     unsigned long long peak;         // largest output + active count seen in the layer
     unsigned long long n_in;         // |O| entering the layer (captured programs)
+    double dropped_sq;               // sum of c^2 over the strings truncation removed
     unsigned int range_cursor;       // next CTA range of the unit kernel
     int pass;                        // chunk pass in progress
     unsigned int err;                // ERR_* bits
@@ -82,6 +83,7 @@ struct ProgramStats {
     unsigned long long pairs_two;
     unsigned long long passes;       // chunk passes of all X layers
     unsigned long long x_layers;     // X layers completed
+    double dropped_sq;               // sum of c^2 of the truncated strings (with norm tracking)
 };
 
 // Per-problem rotation table of a batched X layer: entry p * MAX_QUBITS + q
@@ -100,6 +102,8 @@ struct RxRun {
     uint32_t dbits32;        // threshold as FP32 magnitude bits: smallest float >= delta
     uint64_t dbits64;        // threshold as FP64 magnitude bits
     double delta;            // absolute truncation threshold
+    int32_t track_norm;      // 1: add c^2 of every string truncation removes to Counters::dropped_sq
+    int32_t pad;
     RotTable tab;            // batched contexts: per-problem angles (else null)
     double cs[MAX_QUBITS];   // cos(theta_q), exact at Clifford angles
     double sn[MAX_QUBITS];   // sin(theta_q)
@@ -431,6 +435,24 @@ __device__ __forceinline__ long long warp_append(bool pred, unsigned long long* 
     base = __shfl_sync(FULL_MASK, base, leader);
     if (!pred) return -1;
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+// Sum of a 64-bit value over a full warp (every lane calls it; all lanes
+// receive the total).  Used for event counters that may exceed 2^32.
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned lo = __shfl_xor_sync(FULL_MASK, (unsigned)v, d);
+        const unsigned hi = __shfl_xor_sync(FULL_MASK, (unsigned)(v >> 32), d);
+        v += ((unsigned long long)hi << 32) | lo;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL_MASK, v, d);
+    return v;
 }
 
 // Coefficient types: FP64 (the default) and FP32 (ORQA_FLAG_FP32).  Zero and

@@ -108,11 +108,13 @@ __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrL
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
     const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
+    double drop_sq = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         T c = 0;
         if (i < n) c = sc[i];
         const unsigned long long m = Coef<T>::mag(c);
         const bool keep = (i < n) && (STRICT ? (m > tbits) : keep_t<T>(c, tbits));
+        if (i < n && !keep) drop_sq = fma((double)c, (double)c, drop_sq);
         const long long slot = warp_append(keep, &ctr->n_done);
         if (keep) {
             if (slot < cap) {
@@ -128,6 +130,8 @@ __global__ void __launch_bounds__(256) k_truncate(StrList src, long long n, StrL
             }
         }
     }
+    drop_sq = warp_sum_f64(drop_sq);  // the loop is warp-uniform (n_round and stride are multiples of 32)
+    if ((threadIdx.x & 31) == 0 && drop_sq != 0.0) atomicAdd(&ctr->dropped_sq, drop_sq);
 }
 
 // max |c| as the largest magnitude bit pattern (exact: for non-negative
@@ -155,7 +159,7 @@ template <int W>
 __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, int32_t* table,
                                                       long long table_mask, uint64_t* unit_z, uint64_t* unit_x,
                                                       uint16_t* unit_pid, int32_t* unit_count, int32_t* uid_out,
-                                                      int32_t* rank_out, Counters* ctr) {
+                                                      int32_t* rank_out, Counters* ctr, long long spin_limit) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (n + 31) & ~31ll;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, 
             __syncwarp();
             if (!done) {
                 long long spins = 0;
-                while (v == SLOT_BUSY && spins < SPIN_LIMIT) {
+                while (v == SLOT_BUSY && spins < spin_limit) {
                     v = *((volatile int32_t*)&table[slot]);
                     ++spins;
                 }
@@ -225,6 +229,13 @@ __global__ void __launch_bounds__(256) k_merge_assign(StrList src, long long n, 
             if (my_uid >= 0) rank_out[i] = atomicAdd(&unit_count[my_uid], 1);
         }
     }
+}
+
+// Marks every slot of the merge hash table as being published (a test hook
+// of the bounded wait above: every insertion then waits until its limit).
+__global__ void k_fill_busy(int32_t* table, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        table[i] = SLOT_BUSY;
 }
 
 // Gives every unit a contiguous element range (in arbitrary unit order):
@@ -279,6 +290,7 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
     const long long nu = (long long)*((volatile unsigned long long*)&ctr->n_units);
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (nu + 31) & ~31ll;
+    double drop_sq = 0.0;
     for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n_round; u += stride) {
         double acc = 0.0;
         if (u < nu) {
@@ -304,8 +316,12 @@ __global__ void __launch_bounds__(256) k_merge_reduce(const uint64_t* unit_z,
             }
         } else if (u < nu) {
             atomicAdd(&ctr->dropped, 1ull);
+            const double v64 = (double)v;
+            drop_sq = fma(v64, v64, drop_sq);
         }
     }
+    drop_sq = warp_sum_f64(drop_sq);  // the loop is warp-uniform
+    if ((threadIdx.x & 31) == 0 && drop_sq != 0.0) atomicAdd(&ctr->dropped_sq, drop_sq);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,6 +365,45 @@ __global__ void k_expect_final(const double* partials, int nblocks, double* out,
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(FULL_MASK, acc, d));
     if (lane == 0) *out = ctr->err ? __longlong_as_double(0x7ff8000000000000ll) : acc;  // NaN after an error
+}
+
+// ---------------------------------------------------------------------------
+// Norms of the committed operator: sum of c^2 (FP64, per-block partials in
+// a fixed grid, then added in block order, so the result does not depend on
+// timing) and max |c| (exact, as the largest magnitude bit pattern).  They
+// carry the unitarity invariant of Eq. (update_rule): a rotation keeps sum
+// c^2, so between two layers it falls exactly by the sum of c^2 that the
+// truncation of Eq. (truncation1) removes (up to rounding).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_norms_partial(const T* c, long long cap, const Counters* ctr,
+                                                       double* partials, unsigned long long* max_bits) {
+    __shared__ double red[8];
+    const long long n = min((long long)ctr->n_live, cap);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    unsigned long long m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const T v = c[i];
+        const double d = (double)v;
+        acc = __dadd_rn(acc, __dmul_rn(d, d));
+        m = max(m, Coef<T>::mag(v));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        acc = __dadd_rn(acc, __shfl_down_sync(FULL_MASK, acc, d));
+        m = max(m, __shfl_down_sync(FULL_MASK, m, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = acc;
+        if (m) atomicMax(max_bits, m);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b = __dadd_rn(b, red[k]);
+        partials[blockIdx.x] = b;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -605,6 +660,7 @@ __global__ void k_layer_end_x(Counters* ctr, int cur, uint64_t mask0, uint64_t m
     ps->dropped += ctr->dropped;
     ps->pairs_one += ctr->pairs_one;
     ps->pairs_two += ctr->pairs_two;
+    ps->dropped_sq += ctr->dropped_sq;
     ps->passes += (unsigned long long)ctr->pass;
     ps->x_layers += 1;
 }

@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
     const long long tile = (long long)blockDim.x * SPLIT_ITEMS;
     const unsigned long long dbits = Coef<T>::threshold(run);
     const T* __restrict__ sc = reinterpret_cast<const T*>(src.c);
-    unsigned my_drop = 0;
+    unsigned long long my_drop = 0;
+    double my_drop_sq = 0.0;
     for (long long t0 = (long long)blockIdx.x * tile; t0 < n; t0 += (long long)gridDim.x * tile) {  // block-uniform
         uint64_t z[SPLIT_ITEMS][W];
         T c[SPLIT_ITEMS];
@@ -149,7 +150,11 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
             kind[k] = act ? 2 : (keep ? 1 : 0);
             nd += kind[k] == 1;
             na += kind[k] == 2;
-            my_drop += kind[k] == 0;
+            if (kind[k] == 0) {
+                my_drop += 1;
+                const double cd = (double)c[k];
+                my_drop_sq = fma(cd, cd, my_drop_sq);
+            }
         }
         int total;
         const int pre = block_scan_exclusive(nd | (na << 16), warp_tot, total);
@@ -192,10 +197,12 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
         }
         __syncthreads();  // s_base is rewritten by the next tile
     }
-    const unsigned wd = __reduce_add_sync(FULL_MASK, my_drop);
+    const unsigned long long wd = warp_sum64(my_drop);
+    const double wsq = warp_sum_f64(my_drop_sq);
     if ((threadIdx.x & 31) == 0 && wd) {
-        atomicAdd(&ctr->dropped, (unsigned long long)wd);
-        atomicAdd(&ctr->split_dropped, (unsigned long long)wd);
+        atomicAdd(&ctr->dropped, wd);
+        atomicAdd(&ctr->split_dropped, wd);
+        atomicAdd(&ctr->dropped_sq, wsq);
     }
 }
 
@@ -203,14 +210,16 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
 // just written becomes the active list of the next pass.  With use_cond it
 // also sets the condition of the enclosing graph loop (another pass is
 // needed iff strings are active and no error was raised).
-__global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHandle cond, int use_cond) {
+// pass_limit (at most MAX_PASSES) bounds the loop.
+__global__ void k_pass_advance(Counters* ctr, int first, cudaGraphConditionalHandle cond, int use_cond,
+                               int pass_limit) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const unsigned long long na = ctr->n_next;
     ctr->n_active = na;
     ctr->n_next = 0;
     ctr->range_cursor = 0;
     ctr->pass = first ? 0 : ctr->pass + 1;
-    if (na > 0 && ctr->pass >= MAX_PASSES) atomicOr(&ctr->err, ERR_PASS_LIMIT);  // bounds the loop
+    if (na > 0 && ctr->pass >= pass_limit) atomicOr(&ctr->err, ERR_PASS_LIMIT);
     const unsigned long long pk = ctr->n_done + na;
     if (pk > ctr->peak) ctr->peak = pk;
     if (use_cond) cudaGraphSetConditional(cond, (na > 0 && ctr->err == 0) ? 1u : 0u);
@@ -608,6 +617,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         S.srot[t] = Coef<T>::rot(run, 0u, t);  // one read of the parameter table per qubit
     }
     unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
+    double my_drop_sq = 0.0;
+    const bool track = run.track_norm != 0;
     // The work items are sub-ranges; the next one (claiming a new range when
     // the current range is done) is prepared by warp LB_WARPS - 1 while the
     // other warps work on the current one's units, so the latency of the
@@ -821,6 +832,10 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
+                if (track) {  // block-uniform: the invariant check of the norm bookkeeping
+                    const double da = ka ? 0.0 : (double)na, db = kb ? 0.0 : (double)nb;
+                    my_drop_sq = fma(da, da, fma(db, db, my_drop_sq));
+                }
                 S.dense[ur][la] = na;
                 S.dense[ur][lb] = nb;
                 // occupancy of the pair before (both, or the present member) and after
@@ -919,13 +934,15 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         __syncwarp();
     }
     }
-    const unsigned nb = __reduce_add_sync(FULL_MASK, (unsigned)my_branch);
-    const unsigned nd = __reduce_add_sync(FULL_MASK, (unsigned)my_drop);
+    const unsigned long long nb = warp_sum64(my_branch);
+    const unsigned long long nd = warp_sum64(my_drop);
+    const double nsq = track ? warp_sum_f64(my_drop_sq) : 0.0;
     if (lane == 0 && (nb | nd)) {
-        atomicAdd(&ctr->branch_events, (unsigned long long)nb);
-        atomicAdd(&ctr->dropped, (unsigned long long)nd);
+        atomicAdd(&ctr->branch_events, nb);
+        atomicAdd(&ctr->dropped, nd);
         atomicAdd(&ctr->pairs_one, my_one);
         atomicAdd(&ctr->pairs_two, my_two);
+        if (track) atomicAdd(&ctr->dropped_sq, nsq);
     }
     __syncthreads();
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)

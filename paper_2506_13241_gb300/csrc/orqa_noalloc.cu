@@ -104,6 +104,21 @@ cudaError_t scratch_for_current_device(double** out) {
     return cudaSuccess;
 }
 
+// True iff p is device (or managed) memory that the current device can read
+// and is 8-byte aligned: a host pointer or an odd address would otherwise
+// reach the kernels and fault the GPU instead of returning ORQA_EINVAL.
+bool device_readable(const void* p, int dev) {
+    if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return false;
+    const cudaError_t prior = cudaPeekAtLastError();
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        if (prior == cudaSuccess) cudaGetLastError();  // clear only the failed query's own error
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" orqa_status orqa_expect_noalloc(int32_t n_qubits, int64_t n, const uint64_t* x, const double* c,
@@ -115,6 +130,9 @@ extern "C" orqa_status orqa_expect_noalloc(int32_t n_qubits, int64_t n, const ui
         *out = 0.0;
         return ORQA_OK;
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ORQA_ECUDA;
+    if (!device_readable(x, dev) || !device_readable(c, dev)) return ORQA_EINVAL;
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return ORQA_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -124,7 +142,8 @@ extern "C" orqa_status orqa_expect_noalloc(int32_t n_qubits, int64_t n, const ui
     else
         k_expect_tiles<2><<<n_tiles, NOALLOC_THREADS, 0, s>>>(x, c, n, scratch);
     k_expect_tiles_total<<<1, NOALLOC_THREADS, 0, s>>>(scratch, n_tiles);
-    if (cudaGetLastError() != cudaSuccess) return ORQA_ECUDA;
+    // peek, so that an error is left for its owner to see
+    if (cudaPeekAtLastError() != cudaSuccess) return ORQA_ECUDA;
     if (cudaMemcpyAsync(out, scratch + NOALLOC_MAX_TILES, sizeof(double), cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
         return ORQA_ECUDA;

@@ -30,7 +30,9 @@ EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_se
             "orqa_workspace_bytes_batch", "orqa_set_operator_batch", "orqa_apply_layer_batch",
             "orqa_expect_batch", "orqa_problem_sizes", "orqa_export_batch",
             "orqa_run_program", "orqa_get_tuning", "orqa_set_tuning", "orqa_autotune",
-            "orqa_apply_pauli_rotation", "orqa_histogram"]
+            "orqa_apply_pauli_rotation", "orqa_histogram", "orqa_set_norm_tracking", "orqa_debug_set"]
+ORQA_DEBUG_SPIN_LIMIT, ORQA_DEBUG_POISON_MERGE_TABLE, ORQA_DEBUG_MERGE_TABLE_SLOTS = 1, 2, 3
+ORQA_DEBUG_PASS_LIMIT, ORQA_DEBUG_BUCKET_SHIFT = 4, 5
 ORQA_NOALLOC_MAX_STRINGS = 1 << 27
 ORQA_MAX_PROBLEMS = 4096
 
@@ -61,7 +63,8 @@ class orqa_stats_t(ctypes.Structure):
                 ("last_layer_peak", ctypes.c_int64), ("string_gate_updates", ctypes.c_int64),
                 ("branch_events", ctypes.c_int64), ("dropped", ctypes.c_int64),
                 ("pair_updates_one", ctypes.c_int64), ("pair_updates_two", ctypes.c_int64),
-                ("chunk_passes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("chunk_passes", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("sum_sq", ctypes.c_double), ("max_abs", ctypes.c_double), ("dropped_sum_sq", ctypes.c_double)]
 
 
 class orqa_kernel_profile(ctypes.Structure):
@@ -147,6 +150,10 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_apply_pauli_rotation.argtypes = [vp, vp, vp, dp, dp, i64p]
         lib.orqa_histogram.restype = i32
         lib.orqa_histogram.argtypes = [vp, i32, dp, i64p, dpp]
+        lib.orqa_set_norm_tracking.restype = i32
+        lib.orqa_set_norm_tracking.argtypes = [vp, i32]
+        lib.orqa_debug_set.restype = i32
+        lib.orqa_debug_set.argtypes = [vp, i32, i64]
         _lib = lib
     return _lib
 
@@ -389,6 +396,14 @@ def orqa_stats(ctx) -> dict:
     return {name: getattr(s, name) for name, _ in orqa_stats_t._fields_ if name != "pad"}
 
 
+def orqa_set_norm_tracking(ctx, on: bool):
+    _check(ctx, library().orqa_set_norm_tracking(ctx, 1 if on else 0))
+
+
+def orqa_debug_set(ctx, knob: int, value: int):
+    _check(ctx, library().orqa_debug_set(ctx, int(knob), int(value)))
+
+
 def orqa_profile_count() -> int:
     return int(library().orqa_profile_count())
 
@@ -537,6 +552,12 @@ class Context:
 
     def stats(self) -> dict:
         return orqa_stats(self.ctx)
+
+    def set_norm_tracking(self, on: bool = True):
+        orqa_set_norm_tracking(self.ctx, on)
+
+    def debug_set(self, knob: int, value: int):
+        orqa_debug_set(self.ctx, knob, value)
 
     def profile(self) -> list:
         return [orqa_profile(self.ctx, k) for k in range(orqa_profile_count())]

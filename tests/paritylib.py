@@ -60,3 +60,28 @@ def assert_bit_exact(gpu, ora, what=""):
             what, bad.size, bad[0], gv[bad[0]], ov[bad[0]])
 
 
+
+
+def codes_to_planes(codes: np.ndarray, W: int):
+    """x/z planes [N, W] from per-site codes [N, n] (z = high bit, x = high
+    xor low of the paper's code)."""
+    N, n = codes.shape
+    x = np.zeros((N, W), dtype=np.uint64)
+    z = np.zeros((N, W), dtype=np.uint64)
+    for q in range(n):
+        w, b = divmod(q, 64)
+        hi = (codes[:, q] >> 1) & 1
+        lo = codes[:, q] & 1
+        x[:, w] |= (hi ^ lo).astype(np.uint64) << np.uint64(b)
+        z[:, w] |= hi.astype(np.uint64) << np.uint64(b)
+    return x, z
+
+
+def canonical_key_order(x: np.ndarray, z: np.ndarray, problem=None):
+    """Row order of the canonical export: ascending by x words from the
+    highest to the lowest, then z words likewise (problem index first)."""
+    W = x.shape[1]
+    keys = [z[:, w] for w in range(W)] + [x[:, w] for w in range(W)]
+    if problem is not None:
+        keys.append(np.asarray(problem))
+    return np.lexsort(keys)

@@ -80,7 +80,7 @@ def test_gate_array_marshalling():
     assert (arr[1].kind, arr[1].q0, arr[1].q1) == (orqa.ORQA_RZZ, 1, 2)
     assert ctypes.sizeof(orqa.orqa_gate) == 24
     assert ctypes.sizeof(orqa.orqa_config) == 48
-    assert ctypes.sizeof(orqa.orqa_stats_t) == 72
+    assert ctypes.sizeof(orqa.orqa_stats_t) == 96
     assert ctypes.sizeof(orqa.orqa_layer_desc) == 24
     assert ctypes.sizeof(orqa.orqa_tuning) == 16
 
@@ -141,6 +141,8 @@ def test_null_context_is_rejected_before_any_cuda_call(lib):
     assert lib.orqa_autotune(None, desc, 1, 1, 0.0, 1, ctypes.byref(t), None) == E
     assert lib.orqa_stats(None, None) == E
     assert lib.orqa_profile(None, 0, None) == E
+    assert lib.orqa_set_norm_tracking(None, 1) == E
+    assert lib.orqa_debug_set(None, orqa.ORQA_DEBUG_PASS_LIMIT, 1) == E
 
 
 def test_noalloc_rejects_bad_sizes_before_any_cuda_call(lib):

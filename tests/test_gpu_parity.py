@@ -126,8 +126,12 @@ def test_relative_truncation_random(orqa, oracle_mod):
     # relative merge_truncate: drop |c| <= 0.05 max|c| of the merged set
     mx = op.max_abs()
     op.truncate(0.0)
-    ref = {k: v for k, v in op.as_dict().items() if abs(v) > 0.05 * mx}
-    assert len(ctx) == len(ref) <= keys_before
+    ref = oracle_mod.Oracle(n)
+    for k, v in op.as_dict().items():
+        if abs(v) > 0.05 * mx:
+            ref.add(k, v)
+    assert 0 < len(ref) < keys_before
+    assert_bit_exact(gpu_canonical(ctx, n), oracle_canonical(ref, n), "relative merge_truncate")
 
 
 @pytest.mark.parametrize("delta", [1e-4, 1e-5])

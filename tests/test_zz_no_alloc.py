@@ -52,3 +52,13 @@ def test_expect_noalloc_limits():
     with pytest.raises(orqa.OrqaError) as ei:
         orqa.orqa_expect_noalloc(12, orqa.ORQA_NOALLOC_MAX_STRINGS + 1, x_d.data_ptr(), c_d.data_ptr())
     assert ei.value.status == orqa.ORQA_ECAPACITY
+    # host memory and misaligned addresses are refused before any launch
+    x_h = np.zeros(2, dtype=np.uint64)
+    c_h = np.ones(1, dtype=np.float64)
+    for xp, cp in ((x_h.ctypes.data, c_d.data_ptr()), (x_d.data_ptr(), c_h.ctypes.data),
+                   (x_d.data_ptr() + 4, c_d.data_ptr()), (x_d.data_ptr(), c_d.data_ptr() + 4)):
+        with pytest.raises(orqa.OrqaError) as ei:
+            orqa.orqa_expect_noalloc(12, 1, xp, cp)
+        assert ei.value.status == orqa.ORQA_EINVAL
+    # the refusals leave no CUDA error behind: a valid call still works
+    assert orqa.orqa_expect_noalloc(12, 1, x_d.data_ptr(), c_d.data_ptr()) == 1.0
