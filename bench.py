@@ -55,6 +55,9 @@ def parse_args(argv=None):
                     help="sweep workloads: pick the launch tuning by measurement before warm-up")
     ap.add_argument("--compare-plain", action="store_true",
                     help="sweep workloads: also time the plain FP64 path, one problem after another")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed evolutions: no norm invariants, delta sequence, end-to-end run or "
+                         "sweep comparison (for profiler runs)")
     return ap.parse_args(argv)
 
 
@@ -161,12 +164,12 @@ def make_gpu_runner(wl, capacity, profile=True, fp32=False):
 
     fp64 = {"one": 0, "two": 0, "branch": 0}  # pair updates and branch events of the timed steps
 
-    def evolve():
+    def evolve(d=delta, steps=wl["steps"]):
         updates, mags, peak = 0, [], 0
-        for _ in range(wl["steps"]):
+        for _ in range(steps):
             for layer in layers:
-                B.orqa_apply_layer(ctx.ctx, layer, delta)
-                s = B.orqa_stats(ctx.ctx)
+                B.orqa_apply_layer(ctx.ctx, layer, d)
+                s = B.orqa_counters(ctx.ctx)  # host counters only: no device work in the timed loop
                 updates += s["string_gate_updates"]
                 peak = max(peak, s["last_layer_peak"])
                 fp64["one"] += s["pair_updates_one"]
@@ -175,18 +178,49 @@ def make_gpu_runner(wl, capacity, profile=True, fp32=False):
             mags.append(B.orqa_expect(ctx.ctx))
         return updates, mags, peak
 
-    def step_device():
+    def step_device(d=delta, steps=wl["steps"]):
         ctx.set_operator_device(x_d, z_d, c_d)
-        return evolve()
+        return evolve(d, steps)
 
     def step_host():
         B.orqa_set_operator(ctx.ctx, x_p.numpy().view(np.uint64), z_p.numpy().view(np.uint64),
                             c_p.numpy())
         return evolve()
 
+    def step_invariants():
+        """One evolution with the norm bookkeeping: after every layer, sum c^2
+        before minus sum c^2 after must equal the sum of c^2 the truncation
+        removed (each gate is an orthogonal map on every pair of strings).
+        Then the first steps at delta = 0, where sum c^2 must stay 1."""
+        ctx.set_norm_tracking(True)
+        ctx.set_operator_device(x_d, z_d, c_d)
+        prev = B.orqa_stats(ctx.ctx)["sum_sq"]
+        norm0 = prev
+        worst, layers_checked, per_step = 0.0, 0, []
+        for _ in range(wl["steps"]):
+            for layer in layers:
+                B.orqa_apply_layer(ctx.ctx, layer, delta)
+                s = B.orqa_stats(ctx.ctx)
+                worst = max(worst, abs(prev - s["sum_sq"] - s["dropped_sum_sq"]) / norm0)
+                layers_checked += 1
+                prev = s["sum_sq"]
+            per_step.append(prev)
+        ctx.set_operator_device(x_d, z_d, c_d)
+        exact, exact_steps = 0.0, 0
+        for _ in range(min(4, wl["steps"])):
+            for layer in layers:
+                B.orqa_apply_layer(ctx.ctx, layer, 0.0)
+                exact = max(exact, abs(B.orqa_stats(ctx.ctx)["sum_sq"] - norm0) / norm0)
+            exact_steps += 1
+        ctx.set_norm_tracking(False)
+        return {"max_rel_norm_gap": worst, "steps_checked": wl["steps"], "layers_checked": layers_checked,
+                "sum_sq_per_step": per_step,
+                "delta0_max_rel_norm_change": exact, "delta0_steps": exact_steps,
+                "check": "|sum c^2 before - sum c^2 after - dropped sum c^2| / sum c^2 at t=0, per layer"}
+
     h2d = x_h.nbytes + z_h.nbytes + c_h.nbytes
     d2h = 8 * wl["steps"]
-    return ctx, step_device, step_host, h2d, d2h, fp64
+    return ctx, step_device, step_host, h2d, d2h, fp64, step_invariants
 
 
 def run_gpu(args, wl, rank, world):
@@ -194,7 +228,8 @@ def run_gpu(args, wl, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     capacity = int(args.capacity) if args.capacity else default_capacity(wl)
-    ctx, step_dev, step_host, h2d, d2h, fp64 = make_gpu_runner(wl, capacity, fp32=(args.precision == "fp32"))
+    ctx, step_dev, step_host, h2d, d2h, fp64, step_inv = make_gpu_runner(wl, capacity,
+                                                                         fp32=(args.precision == "fp32"))
     stream = ctx.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -203,8 +238,12 @@ def run_gpu(args, wl, rank, world):
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step_dev()
+    invariants = None
+    for k in range(args.warmup):
+        if k == 0 and not args.no_extras and wl["delta"] > 0:
+            invariants = step_inv()  # the first warm-up evolution checks the norm bookkeeping
+        else:
+            step_dev()
     torch.cuda.synchronize()
     ctx.profile_reset()
     fp64["one"] = fp64["two"] = fp64["branch"] = 0
@@ -230,9 +269,10 @@ def run_gpu(args, wl, rank, world):
     clk = clocks.stop()
     prof = ctx.profile()
     fp64_ops = 2 * fp64["one"] + 6 * fp64["two"]
+    branch_events = fp64["branch"]
     # end to end through the public API with host buffers
     e2e_s, e2e_updates = 0.0, 0
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(max(1, min(args.steps, 2)) if not args.no_extras else 0):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -240,10 +280,32 @@ def run_gpu(args, wl, rank, world):
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
         e2e_updates += upd
+    deltas = None
+    if not args.no_extras and wl["delta"] > 0:
+        deltas = delta_sequence(wl, mags, step_dev)
     times, sums = reduce_over_ranks([total_ms, e2e_s], [total_updates, e2e_updates], "cuda")
     return dict(total_ms=times[0], updates=sums[0], mags=mags, peak=peak, clocks=clk,
                 prof=prof, e2e_s=times[1], e2e_updates=sums[1], h2d=h2d, d2h=d2h,
-                capacity=capacity, fp64_ops=fp64_ops, branch_events=fp64["branch"])
+                capacity=capacity, fp64_ops=fp64_ops, branch_events=branch_events,
+                invariants=invariants, delta_sequence=deltas)
+
+
+def delta_sequence(wl, mags, step_dev):
+    """Parity beyond the oracle's reach: the same evolution at two larger
+    thresholds (delta x 10/7 and x 20/7; 5e-6 and 1e-5 for delta = 3.5e-6).
+    As delta falls the truncation error falls, so the differences between
+    neighbouring thresholds should shrink step by step."""
+    d0 = wl["delta"]
+    seq = [d0, d0 * 10 / 7, d0 * 20 / 7]
+    runs = [list(mags)]
+    for d in seq[1:]:
+        _, m, _ = step_dev(d)
+        runs.append(m)
+    near = [abs(a - b) for a, b in zip(runs[0], runs[1])]
+    far = [abs(a - b) for a, b in zip(runs[1], runs[2])]
+    return {"deltas": seq, "magnetization": runs, "max_abs_diff": [max(near), max(far)],
+            "steps_closer_at_smaller_delta": sum(1 for a, b in zip(near, far) if a <= b),
+            "steps": len(near)}
 
 
 def reduce_over_ranks(times, counts, device="cpu"):
@@ -288,30 +350,54 @@ def fp64_entry(prof, fp64_ops, sm_mhz):
             "peak_note": "2 FP64 lanes/clock/SM x 152 SMs x median SM clock (ncu peak_sustained)"}
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
-# over the kernel's launches) from one ncu capture of the default command on
-# the current kernels; the command and the per-kernel table are in the
-# launch-list summary under profiles/.  Valid only while the kernel and the
-# workload are unchanged.
-MEASURED_TRAFFIC = {("heavyhex_t=20_delta=3.5e-6", "unit_local"): 7.217e10}
+# DRAM traffic of the unit kernel per branch event it processes, from one
+# ncu capture scoped to that kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum over all its launches of one evolution of a
+# few-GB heavy-hex case, divided by that evolution's branch events); the
+# command and figures are in profiles/.  traffic = this ratio x the branch
+# events of an average launch here.  Valid only while the kernel is
+# unchanged: None until it has been measured on the current kernel.
+UNIT_DRAM_BYTES_PER_BRANCH = None
+UNIT_DRAM_SOURCE = "profiles/unit_kernel_traffic_heavyhex_t8_delta3e-5.md"
 
 
-def roofline_entry(prof, steps, workload=None):
+def roofline_entry(prof, steps, workload=None, precision="fp64", n_qubits=127):
+    """The dominant kernel against the measured HBM bandwidth.  `achieved`
+    divides the kernel's share of the method's traffic floor (per X gate: 8
+    bytes of z per string tested, and per branch event the string's record
+    read, the child record and the parent's c written and a merge that
+    meets and writes both once -- 4R + 8 = 168 bytes at 127 qubits in FP64)
+    by the CUDA-event time of its launches; `frac_pass_model` does the same
+    with the bytes of this implementation's pass structure."""
     peak_gbs, peak_src = measured_peaks()
     timed = [p for p in prof if p["launches"] > 0 and p["ms"] > 0]
     if not timed:
         return None
     dom = max(timed, key=lambda p: p["ms"])
-    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
-            "peak": peak_gbs, "peak_source": peak_src, "unit": "GB/s",
-            "frac": round(achieved / peak_gbs, 4), "traffic": MEASURED_TRAFFIC.get((workload, dom["name"])),
-            "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"],
-            "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
-            "share_of_kernel_time": round(dom["ms"] / sum(p["ms"] for p in timed), 4),
-            "kernels": {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
-                                    "GB/s": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)}
-                        for p in timed}}
+    secs = dom["ms"] * 1e-3
+    floor_b = dom.get("floor_bytes", 0.0)
+    achieved = floor_b / secs / 1e9
+    pass_achieved = dom["bytes"] / secs / 1e9
+    entry = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+             "peak": peak_gbs, "peak_source": peak_src, "unit": "GB/s",
+             "frac": round(achieved / peak_gbs, 4),
+             "traffic": None, "traffic_source": None,
+             "frac_pass_model": round(pass_achieved / peak_gbs, 4), "achieved_pass_model": round(pass_achieved, 1),
+             "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"],
+             "algorithmic_bytes_per_launch": floor_b / dom["launches"],
+             "pass_model_bytes_per_launch": dom["bytes"] / dom["launches"],
+             "share_of_kernel_time": round(dom["ms"] / sum(p["ms"] for p in timed), 4),
+             "kernels": {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                                     "floor_GB/s": round(p.get("floor_bytes", 0.0) / (p["ms"] * 1e-3) / 1e9, 1),
+                                     "pass_model_GB/s": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)}
+                         for p in timed}}
+    if dom["name"] == "unit_local" and UNIT_DRAM_BYTES_PER_BRANCH and floor_b > 0:
+        R = 16 * (1 if n_qubits <= 64 else 2) + (4 if precision == "fp32" else 8)
+        per_branch = 4 * R + (4 if precision == "fp32" else 8)
+        branches_per_launch = floor_b / per_branch / dom["launches"]
+        entry["traffic"] = UNIT_DRAM_BYTES_PER_BRANCH * branches_per_launch
+        entry["traffic_source"] = UNIT_DRAM_SOURCE + " (DRAM bytes per branch event x branch events per launch)"
+    return entry
 
 
 # ---------------------------------------------------------------------------
@@ -496,7 +582,7 @@ def run_plain_sweep(wl, capacity):
         for t in range(steps):
             for layer in layers:
                 B.orqa_apply_layer(ctx.ctx, layer, delta)
-                updates += B.orqa_stats(ctx.ctx)["string_gate_updates"]
+                updates += B.orqa_counters(ctx.ctx)["string_gate_updates"]
             mags[t, p] = B.orqa_expect(ctx.ctx)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
@@ -559,7 +645,7 @@ def run_sweep(args, wl, rank, world):
             e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
-        updates += ctx.stats()["string_gate_updates"]
+        updates += B.orqa_counters(ctx.ctx)["string_gate_updates"]
     torch.cuda.synchronize()
     clk = clocks.stop()
     st = ctx.stats()
@@ -656,6 +742,67 @@ def main_sweep(args, world, rank):
         dist.destroy_process_group()
 
 
+SWEEP_BOUND = 1e-6  # |Delta M_t| the precision form should stay within
+
+
+def sweep_comparison(steps_timed=2):
+    """The batched theta x observable sweep (32 angles in [0, pi/2] x Z-strings
+    of weight 1, 3, 17 around qubit 62, 10 Trotter steps, delta = 1e-4) in
+    the FP32-compensated batched form (one captured graph per sweep) against
+    the plain FP64 path (one problem after another, per-layer calls): the
+    speed-up and max over the problems of |Delta M_t| per Trotter step."""
+    import gc
+
+    import numpy as np
+    import torch
+    from paper_2506_13241_gb300 import orqa as B
+    gc.collect()
+    torch.cuda.empty_cache()
+    wl = sweep_from_name("sweep")
+    n, P, steps, delta = wl["n"], len(wl["problems"]), wl["steps"], wl["delta"]
+    zz, xx = wl["layers"]
+    theta = np.array([[wl["theta"][p]] * len(xx) for p in range(P)])
+    ctx = B.Context(n, int(4e8), fp32=True, problems=P)
+    ctx.set_tuning(bucket_density=32, grid_per_sm=8)  # the autotuner's choice for this sweep
+    prog = ctx.program([(zz, False, None), (xx, True, theta)])
+    x, z, c, pid = sweep_inputs(wl)
+    stream = ctx.stream
+
+    def step():
+        B.orqa_set_operator_batch(ctx.ctx, x, z, c, pid)
+        return ctx.run_program(prog, steps, delta)
+
+    mags = step()  # captures the graph
+    ms, updates = 0.0, 0
+    for _ in range(steps_timed):
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mags = step()
+            e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        updates += B.orqa_counters(ctx.ctx)["string_gate_updates"]
+    del ctx
+    gc.collect()
+    torch.cuda.empty_cache()
+    plain, pm = run_plain_sweep(wl, int(6e7))
+    per_step = np.abs(np.asarray(mags) - pm).max(axis=1)
+    within = 0
+    for v in per_step:
+        if v > SWEEP_BOUND:
+            break
+        within += 1
+    batched = updates / (ms * 1e-3)
+    return {"workload": "sweep: %d angles x 3 observables, %d steps, delta %g" % (P // 3, steps, delta),
+            "batched_fp32": {"value": batched, "unit": UNIT, "ms_per_sweep": ms / steps_timed},
+            "plain_fp64_sequential": plain, "speedup": batched / plain["value"],
+            "max_abs_dM_per_step": [float(v) for v in per_step], "bound": SWEEP_BOUND,
+            "steps_within_bound": within, "bound_met": within == steps,
+            "reference": "the plain FP64 path (its operators equal the CPU oracle's bit for bit in the tests)"}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.workload.startswith("sweep") and args.impl != "reference":
@@ -686,25 +833,32 @@ def main(argv=None):
     total_updates = res["updates"]  # summed over the ranks' replicas
     secs = res["total_ms"] * 1e-3
     value = total_updates / secs
-    e2e_value = res["e2e_updates"] / res["e2e_s"]
+    e2e_value = res["e2e_updates"] / res["e2e_s"] if res["e2e_s"] > 0 else None
     launches = kernel_launches(res["prof"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic", "config": workload_config(wl, args.precision),
-            "roofline": roofline_entry(res["prof"], args.steps, wl["name"]),
+            "roofline": roofline_entry(res["prof"], args.steps, wl["name"], args.precision, wl["n"]),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
             "gpu_launches": launches, "clocks": res["clocks"],
             "magnetization": res["mags"], "peak_strings": res["peak"], "capacity": res["capacity"]}
     line["fp64"] = fp64_entry(res["prof"], res["fp64_ops"], res["clocks"].get("sm_mhz"))
+    if res["invariants"] is not None:
+        line["invariants"] = res["invariants"]
+    if res["delta_sequence"] is not None:
+        line["delta_sequence"] = res["delta_sequence"]
     # secondary metric: anticommuting (string, gate) pairs per second (rank 0's replica)
     line["branch_events_per_s"] = res["branch_events"] / (res["total_ms"] * 1e-3) * world
     if args.precision == "fp32":
         # The precision form's error per step against the GPU FP64 path on
         # the same workload (one untimed evolution after the timed run).
         line["magnetization_error_vs_gpu_fp64"] = error_entry(res["mags"], fp64_magnetization(wl, res["capacity"]))
+    if not args.no_extras and world == 1 and wl["n"] == 127 and args.precision == "fp64":
+        res["prof"] = None
+        line["sweep"] = sweep_comparison()
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is an N = 1 figure
         cb = cpu_baseline(wl, args.cpu_seconds)
         om = cb.pop("magnetization")

@@ -126,14 +126,24 @@ typedef struct {
                                  X layers ran without orqa_set_norm_tracking */
 } orqa_stats_t;
 
-/* Per-kernel launch profile (ORQA_FLAG_PROFILE).  bytes is the kernel's
- * algorithmic DRAM traffic: the bytes its inputs and outputs must move at
- * least once (not counting hash-probe misses or cache effects). */
+/* Per-kernel launch profile (ORQA_FLAG_PROFILE).
+ *   bytes: the kernel's algorithmic DRAM traffic in this implementation's
+ *     pass structure: the bytes its inputs and outputs must move at least
+ *     once (not counting hash-probe misses or cache effects).
+ *   floor_bytes: the kernel's share of the method's own traffic floor, the
+ *     same for any implementation: per X gate 8 bytes of z per string tested
+ *     and, per anticommuting string, its record read, the child record and
+ *     the parent's coefficient written and a merge that meets and writes
+ *     both once (4R + sizeof(c) bytes per branch event, R the bytes of one
+ *     string, charged to the unit kernel, which does all branching); per ZZ
+ *     layer R read plus the z planes and c written per string; per
+ *     expectation the x planes and c read.  0 for kernels without one. */
 typedef struct {
     char name[32];
     int64_t launches;
     double ms;               /* summed CUDA-event durations */
-    double bytes;            /* summed algorithmic bytes */
+    double bytes;            /* summed algorithmic bytes (pass structure) */
+    double floor_bytes;      /* summed floor bytes (method) */
 } orqa_kernel_profile;
 
 typedef struct orqa_ctx orqa_ctx;
@@ -230,6 +240,11 @@ orqa_status orqa_histogram(orqa_ctx* ctx, int32_t n_bins, double log10_lo, int64
  * device (8 bytes per string) and waits for the stream; later calls return
  * the cached values. */
 orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out);
+
+/* orqa_stats without the device reduction: the counters of the last call,
+ * with sum_sq and max_abs as cached (NaN if the operator changed since the
+ * last orqa_stats).  For per-layer bookkeeping inside timed loops. */
+orqa_status orqa_counters(orqa_ctx* ctx, orqa_stats_t* out);
 
 /* on = 1: the X-layer kernels also add up the c^2 of every string their
  * truncation removes (orqa_stats_t.dropped_sum_sq), the bookkeeping that
@@ -353,6 +368,41 @@ orqa_status orqa_set_tuning(orqa_ctx* ctx, const orqa_tuning* in);
 orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t n_layers,
                           int32_t repeat, double delta, int32_t trials, orqa_tuning* best,
                           double* best_ms);
+
+/* Sharding one operator over R ranks (one GPU each) by a hash of the z
+ * plane: the multi-device partition of the ORQA method (Sec. II, the
+ * partial operators O^(m) of Eq. eq:Om), with the owner map of Eq.
+ * distributor taken as owner(z), a fixed 64-bit mix of the z words reduced
+ * mod R.  An X rotation flips only x bits, so the strings an X layer can
+ * merge share their z plane and every X layer (branching, merging,
+ * truncation) runs on each rank with no data from another.  A ZZ layer maps
+ * each string to exactly one string with a new z: after it each rank calls
+ * orqa_shard_split, the ranks exchange the records (one all-to-all), and
+ * each calls orqa_shard_append on what it received.  <0|O|0> is the sum of
+ * the ranks' orqa_expect values.  Plain (not batched) contexts only. */
+#define ORQA_SHARD_MAX_RANKS 512
+
+/* owner(z) of n strings: z is a HOST array of n*W words (string-major);
+ * out[i] in [0, n_ranks).  Host-only; the device uses the same function. */
+orqa_status orqa_shard_owner(int32_t n_qubits, int64_t n, const uint64_t* z, int32_t n_ranks, int32_t* out);
+
+/* Moves the strings of the operator whose owner is not `rank` to the DEVICE
+ * buffer `send` (send_cap records of 2W + 1 uint64 words: the x words, the z
+ * words, then the coefficient's bit pattern -- a float in the low 32 bits
+ * in the FP32 form), grouped by destination rank in ascending order;
+ * send_counts (HOST, n_ranks int64) receives the records per destination
+ * (0 for `rank` itself).  The operator keeps its own strings.  ECAPACITY
+ * (nothing moved) if more than send_cap strings leave. */
+orqa_status orqa_shard_split(orqa_ctx* ctx, int32_t n_ranks, int32_t rank, int64_t send_cap, uint64_t* send,
+                             int64_t* send_counts);
+
+/* Appends n records (the format of orqa_shard_split) from the DEVICE buffer
+ * recv to the operator, without merging: the caller guarantees that they
+ * are distinct from each other and from the operator's strings, as the
+ * strings arriving after a ZZ layer are (the layer is a bijection), and
+ * that they were truncated at the same threshold as the operator.
+ * ECAPACITY (nothing appended) if |O| + n exceeds the capacity. */
+orqa_status orqa_shard_append(orqa_ctx* ctx, int64_t n, const uint64_t* recv);
 
 /* Test hooks of the failure paths (not for production use).  Each makes a
  * bounded device-side condition fire without faulting or hanging the GPU,

@@ -15,6 +15,7 @@
 #include "orqa_kernels.cuh"
 #include "orqa_layer.cuh"
 #include "orqa_sort.cuh"
+#include "orqa_shard.cuh"
 
 using namespace orqa;
 
@@ -33,6 +34,7 @@ struct PendingLaunch {
     int kind;
     cudaEvent_t a, b;
     double bytes;
+    double floor_bytes;
 };
 }  // namespace
 
@@ -125,6 +127,7 @@ struct orqa_ctx {
     long long prof_launches[K_COUNT] = {};
     double prof_ms[K_COUNT] = {};
     double prof_bytes[K_COUNT] = {};
+    double prof_floor[K_COUNT] = {};
 
     void drop_programs() {
         for (auto& p : programs) {
@@ -354,7 +357,7 @@ cudaEvent_t take_event(orqa_ctx* ctx) {
 // be filled in once the counters are known.
 int prof_begin(orqa_ctx* ctx, int kind, double bytes) {
     if (!ctx->profile) return -1;
-    PendingLaunch p{kind, take_event(ctx), take_event(ctx), bytes};
+    PendingLaunch p{kind, take_event(ctx), take_event(ctx), bytes, 0.0};
     cudaEventRecord(p.a, ctx->stream);
     ctx->pending.push_back(p);
     return (int)ctx->pending.size() - 1;
@@ -368,6 +371,12 @@ void prof_set_bytes(orqa_ctx* ctx, int rec, double bytes) {
     if (rec >= 0) ctx->pending[rec].bytes = bytes;
 }
 
+// The launch's share of the method's per-gate traffic floor (see
+// orqa_kernel_profile.floor_bytes).
+void prof_set_floor(orqa_ctx* ctx, int rec, double bytes) {
+    if (rec >= 0) ctx->pending[rec].floor_bytes = bytes;
+}
+
 // Call only after the stream has been synchronised.
 void prof_resolve(orqa_ctx* ctx) {
     for (auto& p : ctx->pending) {
@@ -375,6 +384,7 @@ void prof_resolve(orqa_ctx* ctx) {
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             ctx->prof_ms[p.kind] += ms;
             ctx->prof_bytes[p.kind] += p.bytes;
+            ctx->prof_floor[p.kind] += p.floor_bytes;
             ctx->prof_launches[p.kind] += 1;
         }
         ctx->event_pool.push_back(p.a);
@@ -580,6 +590,7 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
         const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T)));
         k_rzz_layer<W, T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->cap, ctx->ctr, l);
         prof_end(ctx, r);
+        prof_set_floor(ctx, r, (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T)));
         LAUNCH_CHECK(ctx);
     }
     ctx->stats.last_layer_in = ctx->n;
@@ -746,9 +757,16 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
     int pass = 0;
+    // per-gate floor of an X gate (8 bytes of z per string tested, then per
+    // anticommuting string its x, z, c read, the child record and the
+    // parent's c written, and a merge that meets and writes both once):
+    // 8 + (R - 8) + R + sizeof(T) + 2R bytes per branch event, charged to the
+    // unit kernel, which does all branching
+    const double floor_per_branch = 4.0 * R + (double)sizeof(T);
     while (h.n_active > 0) {  // ends: k_pass_advance flags an error beyond pass_limit passes
         const long long n_active = (long long)h.n_active;
         const unsigned long long done_before = h.n_done;
+        const unsigned long long branch_before = h.branch_events;
         int r_sc = -1, r_lo = -1;
         // the scatter also clears the bucket counts: its grid covers both
         const long long scatter_work = std::max((n_active + SCATTER_ILP - 1) / SCATTER_ILP, (long long)ctx->n_fine);
@@ -759,6 +777,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
         const double outs = (double)(h.n_done - done_before) + (double)h.n_active;
         prof_set_bytes(ctx, r_sc, (double)n_active * (R + 12.0 + record_bytes(W)));
         prof_set_bytes(ctx, r_lo, (double)n_active * record_bytes(W) + outs * R + (double)h.n_active * 12.0);
+        prof_set_floor(ctx, r_lo, (double)(h.branch_events - branch_before) * floor_per_branch);
         prof_resolve(ctx);
         if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
         ++pass;
@@ -975,6 +994,7 @@ orqa_status enqueue_expect(orqa_ctx* ctx, int cur, long long n_hint, double* dev
         k_expect_partial<W, T><<<EXPECT_BLOCKS, 256, 0, ctx->stream>>>(s, ctx->cap, ctx->ctr, ctx->partials);
         k_expect_final<<<1, 32, 0, ctx->stream>>>(ctx->partials, EXPECT_BLOCKS, dev_out, ctx->ctr);
         prof_end(ctx, r);
+        prof_set_floor(ctx, r, (double)n_hint * (8.0 * W + sizeof(T)));
     }
     LAUNCH_CHECK(ctx);
     return ORQA_OK;
@@ -1444,6 +1464,15 @@ orqa_status orqa_stats(orqa_ctx* ctx, orqa_stats_t* out) {
     return ORQA_OK;
 }
 
+orqa_status orqa_counters(orqa_ctx* ctx, orqa_stats_t* out) {
+    if (!ctx || !out) return ORQA_EINVAL;
+    ctx->stats.n_strings = ctx->n;
+    ctx->stats.sum_sq = ctx->norms_valid ? ctx->norm_sq : std::nan("");
+    ctx->stats.max_abs = ctx->norms_valid ? ctx->norm_max : std::nan("");
+    *out = ctx->stats;
+    return ORQA_OK;
+}
+
 orqa_status orqa_set_norm_tracking(orqa_ctx* ctx, int32_t on) {
     if (!ctx || (on != 0 && on != 1)) return ORQA_EINVAL;
     ctx->track_norm = on != 0;
@@ -1491,6 +1520,7 @@ orqa_status orqa_profile(orqa_ctx* ctx, int32_t index, orqa_kernel_profile* out)
     out->launches = ctx->prof_launches[index];
     out->ms = ctx->prof_ms[index];
     out->bytes = ctx->prof_bytes[index];
+    out->floor_bytes = ctx->prof_floor[index];
     return ORQA_OK;
 }
 
@@ -1500,6 +1530,7 @@ orqa_status orqa_profile_reset(orqa_ctx* ctx) {
         ctx->prof_launches[k] = 0;
         ctx->prof_ms[k] = 0.0;
         ctx->prof_bytes[k] = 0.0;
+        ctx->prof_floor[k] = 0.0;
     }
     return ORQA_OK;
 }
@@ -1907,6 +1938,100 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
     if (best_ms) *best_ms = cur_ms;
     ctx->err.clear();
     return ORQA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sharding by a hash of the z plane (orqa_shard.cuh): placement, the split
+// of the strings another rank owns after a ZZ layer, and their merge-free
+// arrival.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int W, typename T>
+orqa_status shard_split_impl(orqa_ctx* ctx, int R, int rank, long long send_cap, uint64_t* send, int64_t* counts_out) {
+    const long long n = ctx->n;
+    for (int r = 0; r < R; ++r) counts_out[r] = 0;
+    if (n == 0) return ORQA_OK;
+    unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(ctx->partials);
+    unsigned long long* d_cur = d_cnt + SHARD_MAX_RANKS;
+    CUDA_TRY(ctx, cudaMemsetAsync(d_cnt, 0, (size_t)R * 8, ctx->stream));
+    const StrList src = ctx->buf[ctx->cur];
+    k_shard_count<W><<<grid_for(ctx, n), 256, (size_t)R * 4, ctx->stream>>>(src, n, R, d_cnt);
+    LAUNCH_CHECK(ctx);
+    std::vector<unsigned long long> cnt((size_t)R);
+    CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), d_cnt, (size_t)R * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const long long out = n - (long long)cnt[(size_t)rank];
+    if (out > send_cap) {
+        char b[160];
+        snprintf(b, sizeof b, "shard_split: %lld strings leave, send buffer holds %lld", out, send_cap);
+        return fail(ctx, ORQA_ECAPACITY, b);
+    }
+    if (out > 0 && !send) return fail(ctx, ORQA_EINVAL, "shard_split: null send buffer");
+    std::vector<unsigned long long> cur((size_t)R, 0ull);
+    unsigned long long run = 0;
+    for (int r = 0; r < R; ++r) {
+        if (r == rank) continue;
+        cur[(size_t)r] = run;
+        run += cnt[(size_t)r];
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(d_cur, cur.data(), (size_t)R * 8, cudaMemcpyHostToDevice, ctx->stream));
+    if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+    const int keep = (ctx->cur + 1) % 3;
+    k_shard_scatter<W, T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(src, n, R, rank, ctx->buf[keep], d_cur, send,
+                                                                    send_cap, ctx->ctr);
+    LAUNCH_CHECK(ctx);
+    Counters h{};
+    orqa_status st = sync_counters(ctx, &h);
+    if (st != ORQA_OK) return st;
+    if ((st = check_flags(ctx, h, "shard_split")) != ORQA_OK) return st;
+    if ((long long)h.n_done != (long long)cnt[(size_t)rank]) return fail(ctx, ORQA_ECUDA, "shard_split: count mismatch");
+    for (int r = 0; r < R; ++r) counts_out[r] = r == rank ? 0 : (int64_t)cnt[(size_t)r];
+    return host_commit(ctx, keep, (long long)h.n_done);
+}
+
+template <int W, typename T>
+orqa_status shard_append_impl(orqa_ctx* ctx, long long m, const uint64_t* recv) {
+    if (m == 0) return ORQA_OK;
+    k_shard_append<W, T><<<grid_for(ctx, m), 256, 0, ctx->stream>>>(recv, m, ctx->buf[ctx->cur], ctx->n);
+    LAUNCH_CHECK(ctx);
+    return host_commit(ctx, ctx->cur, ctx->n + m);
+}
+
+}  // namespace
+
+extern "C" {
+
+orqa_status orqa_shard_owner(int32_t n_qubits, int64_t n, const uint64_t* z, int32_t n_ranks, int32_t* out) {
+    if (n_qubits < 1 || n_qubits > 128 || n < 0 || n_ranks < 1 || n_ranks > SHARD_MAX_RANKS ||
+        (n > 0 && (!z || !out)))
+        return ORQA_EINVAL;
+    const int W = n_qubits <= 64 ? 1 : 2;
+    for (int64_t i = 0; i < n; ++i) out[i] = shard_owner(z + i * W, W, n_ranks);
+    return ORQA_OK;
+}
+
+orqa_status orqa_shard_split(orqa_ctx* ctx, int32_t n_ranks, int32_t rank, int64_t send_cap, uint64_t* send,
+                             int64_t* send_counts) {
+    if (!ctx) return ORQA_EINVAL;
+    if (n_ranks < 1 || n_ranks > SHARD_MAX_RANKS || rank < 0 || rank >= n_ranks || send_cap < 0 || !send_counts)
+        return fail(ctx, ORQA_EINVAL, "shard_split: bad arguments");
+    if (ctx->P > 1) return fail(ctx, ORQA_ESTATE, "shard_split: not for batched contexts");
+    const orqa_status st = ORQA_DISPATCH(ctx, shard_split_impl, ctx, n_ranks, rank, send_cap, send, send_counts);
+    if (st == ORQA_OK) ctx->err.clear();
+    return st;
+}
+
+orqa_status orqa_shard_append(orqa_ctx* ctx, int64_t n, const uint64_t* recv) {
+    if (!ctx) return ORQA_EINVAL;
+    if (n < 0 || (n > 0 && !recv)) return fail(ctx, ORQA_EINVAL, "shard_append: bad arguments");
+    if (ctx->P > 1) return fail(ctx, ORQA_ESTATE, "shard_append: not for batched contexts");
+    if (ctx->n + n > ctx->cap) return fail(ctx, ORQA_ECAPACITY, "shard_append: result exceeds capacity");
+    const orqa_status st = ORQA_DISPATCH(ctx, shard_append_impl, ctx, n, recv);
+    if (st == ORQA_OK) ctx->err.clear();
+    return st;
 }
 
 }  // extern "C"

@@ -16,7 +16,7 @@
 
 namespace orqa {
 
-constexpr int SHARD_MAX_RANKS = 4096;
+constexpr int SHARD_MAX_RANKS = 512;  // ORQA_SHARD_MAX_RANKS
 
 // Owner rank of a z plane: a 64-bit mix of its words, reduced mod R.  The
 // same code runs on the host (placement) and on the device (exchange).
@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(256) k_shard_count(StrList s, long long n, int
 // go to send[cursor[owner]++] (cursor: the start of each destination's run).
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_shard_scatter(StrList s, long long n, int n_ranks, int rank, StrList keep,
-                                                       unsigned long long* cursor, uint64_t* send, Counters* ctr) {
+                                                       unsigned long long* cursor, uint64_t* send, long long send_cap,
+                                                       Counters* ctr) {
     const long long n_round = (n + 31) & ~31ll;
     const int lane = threadIdx.x & 31;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) k_shard_scatter(StrList s, long long n, i
             o = shard_owner(z, W, n_ranks);
         }
         const long long k = warp_append(live && o == rank, &ctr->n_done);
-        if (live && o == rank) {
+        if (live && o == rank && k < n) {
             store_plane<W>(keep.x, k, x);
             store_plane<W>(keep.z, k, z);
             reinterpret_cast<T*>(keep.c)[k] = c;
@@ -87,6 +88,10 @@ __global__ void __launch_bounds__(256) k_shard_scatter(StrList s, long long n, i
         b = __shfl_sync(FULL_MASK, b, leader);  // every lane takes its group leader's base
         if (out) {
             const long long slot = (long long)b + __popc(peers & ((1u << lane) - 1u));
+            if (slot >= send_cap) {  // only after a count mismatch; never write past the buffer
+                atomicOr(&ctr->err, ERR_OVERFLOW);
+                continue;
+            }
             uint64_t* r = send + slot * (2 * W + 1);
 #pragma unroll
             for (int w = 0; w < W; ++w) {

@@ -30,7 +30,9 @@ EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_se
             "orqa_workspace_bytes_batch", "orqa_set_operator_batch", "orqa_apply_layer_batch",
             "orqa_expect_batch", "orqa_problem_sizes", "orqa_export_batch",
             "orqa_run_program", "orqa_get_tuning", "orqa_set_tuning", "orqa_autotune",
-            "orqa_apply_pauli_rotation", "orqa_histogram", "orqa_set_norm_tracking", "orqa_debug_set"]
+            "orqa_apply_pauli_rotation", "orqa_histogram", "orqa_set_norm_tracking", "orqa_debug_set",
+            "orqa_shard_owner", "orqa_shard_split", "orqa_shard_append", "orqa_counters"]
+ORQA_SHARD_MAX_RANKS = 512
 ORQA_DEBUG_SPIN_LIMIT, ORQA_DEBUG_POISON_MERGE_TABLE, ORQA_DEBUG_MERGE_TABLE_SLOTS = 1, 2, 3
 ORQA_DEBUG_PASS_LIMIT, ORQA_DEBUG_BUCKET_SHIFT = 4, 5
 ORQA_NOALLOC_MAX_STRINGS = 1 << 27
@@ -69,7 +71,7 @@ class orqa_stats_t(ctypes.Structure):
 
 class orqa_kernel_profile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("floor_bytes", ctypes.c_double)]
 
 
 class OrqaError(RuntimeError):
@@ -110,6 +112,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_export.argtypes = [vp, i64, u64p, u64p, dpp, ctypes.POINTER(i64)]
         lib.orqa_stats.restype = i32
         lib.orqa_stats.argtypes = [vp, ctypes.POINTER(orqa_stats_t)]
+        lib.orqa_counters.restype = i32
+        lib.orqa_counters.argtypes = [vp, ctypes.POINTER(orqa_stats_t)]
         lib.orqa_profile_count.restype = i32
         lib.orqa_profile_count.argtypes = []
         lib.orqa_profile.restype = i32
@@ -154,6 +158,12 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.orqa_set_norm_tracking.argtypes = [vp, i32]
         lib.orqa_debug_set.restype = i32
         lib.orqa_debug_set.argtypes = [vp, i32, i64]
+        lib.orqa_shard_owner.restype = i32
+        lib.orqa_shard_owner.argtypes = [i32, i64, vp, i32, vp]
+        lib.orqa_shard_split.restype = i32
+        lib.orqa_shard_split.argtypes = [vp, i32, i32, i64, vp, i64p]
+        lib.orqa_shard_append.restype = i32
+        lib.orqa_shard_append.argtypes = [vp, i64, vp]
         _lib = lib
     return _lib
 
@@ -396,12 +406,41 @@ def orqa_stats(ctx) -> dict:
     return {name: getattr(s, name) for name, _ in orqa_stats_t._fields_ if name != "pad"}
 
 
+def orqa_counters(ctx) -> dict:
+    s = orqa_stats_t()
+    _check(ctx, library().orqa_counters(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in orqa_stats_t._fields_ if name != "pad"}
+
+
 def orqa_set_norm_tracking(ctx, on: bool):
     _check(ctx, library().orqa_set_norm_tracking(ctx, 1 if on else 0))
 
 
 def orqa_debug_set(ctx, knob: int, value: int):
     _check(ctx, library().orqa_debug_set(ctx, int(knob), int(value)))
+
+
+def orqa_shard_owner(n_qubits: int, z: np.ndarray, n_ranks: int) -> np.ndarray:
+    """Owner rank of each string's z plane (z: [N, W] uint64 host array)."""
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    out = np.zeros(max(len(z), 1), dtype=np.int32)
+    st = library().orqa_shard_owner(n_qubits, len(z), z.ctypes.data, n_ranks, out.ctypes.data)
+    if st != ORQA_OK:
+        raise OrqaError(st, "orqa_shard_owner")
+    return out[:len(z)]
+
+
+def orqa_shard_split(ctx, n_ranks: int, rank: int, send_cap: int, send_ptr: int) -> np.ndarray:
+    """Moves the strings other ranks own to the device buffer at send_ptr;
+    returns the records per destination rank."""
+    counts = np.zeros(n_ranks, dtype=np.int64)
+    _check(ctx, library().orqa_shard_split(ctx, n_ranks, rank, send_cap, send_ptr,
+                                           counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return counts
+
+
+def orqa_shard_append(ctx, n: int, recv_ptr: int):
+    _check(ctx, library().orqa_shard_append(ctx, n, recv_ptr))
 
 
 def orqa_profile_count() -> int:
@@ -411,7 +450,8 @@ def orqa_profile_count() -> int:
 def orqa_profile(ctx, index: int) -> dict:
     p = orqa_kernel_profile()
     _check(ctx, library().orqa_profile(ctx, index, ctypes.byref(p)))
-    return {"name": p.name.decode(), "launches": p.launches, "ms": p.ms, "bytes": p.bytes}
+    return {"name": p.name.decode(), "launches": p.launches, "ms": p.ms, "bytes": p.bytes,
+            "floor_bytes": p.floor_bytes}
 
 
 def orqa_profile_reset(ctx):
@@ -552,6 +592,9 @@ class Context:
 
     def stats(self) -> dict:
         return orqa_stats(self.ctx)
+
+    def counters(self) -> dict:
+        return orqa_counters(self.ctx)
 
     def set_norm_tracking(self, on: bool = True):
         orqa_set_norm_tracking(self.ctx, on)

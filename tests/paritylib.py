@@ -85,3 +85,14 @@ def canonical_key_order(x: np.ndarray, z: np.ndarray, problem=None):
     if problem is not None:
         keys.append(np.asarray(problem))
     return np.lexsort(keys)
+
+
+def planes_to_index_words(x: np.ndarray, z: np.ndarray, n: int) -> np.ndarray:
+    """Oracle multi-index words [N, 4] (two bits per site, the paper's code)
+    from x/z planes."""
+    codes = planes_to_codes(x, z, n)
+    keys = np.zeros((x.shape[0], 4), dtype=np.uint64)
+    for q in range(n):
+        w, b = divmod(2 * q, 64)
+        keys[:, w] |= codes[:, q].astype(np.uint64) << np.uint64(b)
+    return keys

@@ -81,6 +81,7 @@ def test_gate_array_marshalling():
     assert ctypes.sizeof(orqa.orqa_gate) == 24
     assert ctypes.sizeof(orqa.orqa_config) == 48
     assert ctypes.sizeof(orqa.orqa_stats_t) == 96
+    assert ctypes.sizeof(orqa.orqa_kernel_profile) == 64
     assert ctypes.sizeof(orqa.orqa_layer_desc) == 24
     assert ctypes.sizeof(orqa.orqa_tuning) == 16
 

@@ -17,17 +17,31 @@ def test_defaults_finish_within_minutes():
 
 
 def test_roofline_entry_uses_the_dominant_kernel():
-    prof = [{"name": "unit_local", "launches": 4, "ms": 40.0, "bytes": 4.0e10},
-            {"name": "bucket_scatter", "launches": 4, "ms": 10.0, "bytes": 2.0e10},
-            {"name": "expect", "launches": 0, "ms": 0.0, "bytes": 0.0}]
+    """frac divides the dominant kernel's share of the method's traffic floor
+    (168 bytes per branch event for the unit kernel at 127 qubits, FP64) by
+    its event time; frac_pass_model uses the pass-structure bytes; traffic
+    is the per-branch-event DRAM ratio of a scoped capture, if measured on
+    the current kernel."""
+    prof = [{"name": "unit_local", "launches": 4, "ms": 40.0, "bytes": 4.0e10, "floor_bytes": 168.0 * 1e8},
+            {"name": "bucket_scatter", "launches": 4, "ms": 10.0, "bytes": 2.0e10, "floor_bytes": 0.0},
+            {"name": "expect", "launches": 0, "ms": 0.0, "bytes": 0.0, "floor_bytes": 0.0}]
     r = bench.roofline_entry(prof, 1, bench.DEFAULT_WORKLOAD)
     peak, _ = bench.measured_peaks()
     assert r["kernel"] == "unit_local" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert abs(r["achieved"] - 1000.0) < 1e-9                     # 4e10 B / 40 ms
-    assert abs(r["frac"] - round(1000.0 / peak, 4)) < 1e-12
-    assert r["traffic"] == bench.MEASURED_TRAFFIC[(bench.DEFAULT_WORKLOAD, "unit_local")]
+    assert abs(r["achieved"] - 420.0) < 1e-9                      # 1.68e10 B / 40 ms
+    assert abs(r["frac"] - round(420.0 / peak, 4)) < 1e-12
+    assert abs(r["achieved_pass_model"] - 1000.0) < 1e-9          # 4e10 B / 40 ms
+    assert abs(r["algorithmic_bytes_per_launch"] - 168.0 * 1e8 / 4) < 1e-3
     assert abs(r["share_of_kernel_time"] - 0.8) < 1e-12
-    assert bench.roofline_entry(prof, 1, "chain12")["traffic"] is None
+    old = bench.UNIT_DRAM_BYTES_PER_BRANCH
+    try:
+        bench.UNIT_DRAM_BYTES_PER_BRANCH = None
+        assert bench.roofline_entry(prof, 1)["traffic"] is None
+        bench.UNIT_DRAM_BYTES_PER_BRANCH = 100.0
+        t = bench.roofline_entry(prof, 1)["traffic"]
+        assert abs(t - 100.0 * 1e8 / 4) < 1e-3                    # 2.5e7 branch events per launch
+    finally:
+        bench.UNIT_DRAM_BYTES_PER_BRANCH = old
 
 
 def test_kernel_launch_count():
