@@ -852,6 +852,7 @@ def main(argv=None):
         line["delta_sequence"] = res["delta_sequence"]
     # secondary metric: anticommuting (string, gate) pairs per second (rank 0's replica)
     line["branch_events_per_s"] = res["branch_events"] / (res["total_ms"] * 1e-3) * world
+    line["branch_events"] = res["branch_events"]  # of the timed evolutions on this rank
     if args.precision == "fp32":
         # The precision form's error per step against the GPU FP64 path on
         # the same workload (one untimed evolution after the timed run).

@@ -719,9 +719,14 @@ orqa_status enqueue_pass(orqa_ctx* ctx, const RxLists& L, const RxRun& run, int 
     prof_end(ctx, *r_sc);
     LAUNCH_CHECK(ctx);
     *r_lo = prof_begin(ctx, K_LOCAL, 0);
-    k_bucket_local<W, T><<<local_grid_n, LB_THREADS, ctx->local_smem, ctx->stream>>>(
-        ctx->records, ctx->foffsets, ctx->range_start, ctx->n_fine, ctx->range_target, ctx->sub_max, run, L.done,
-        L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
+    if (run.track_norm)
+        k_bucket_local<W, T, true><<<local_grid_n, LB_THREADS, ctx->local_smem, ctx->stream>>>(
+            ctx->records, ctx->foffsets, ctx->range_start, ctx->n_fine, ctx->range_target, ctx->sub_max, run, L.done,
+            L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
+    else
+        k_bucket_local<W, T, false><<<local_grid_n, LB_THREADS, ctx->local_smem, ctx->stream>>>(
+            ctx->records, ctx->foffsets, ctx->range_start, ctx->n_fine, ctx->range_target, ctx->sub_max, run, L.done,
+            L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
     prof_end(ctx, *r_lo);
     LAUNCH_CHECK(ctx);
     k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 0, cond, use_cond, ctx->pass_limit);
@@ -1138,6 +1143,25 @@ orqa_status sorted_buffer(orqa_ctx* ctx, int* out_buf) {
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+// Dynamic shared memory of the unit kernel (both instantiations).
+template <int W, typename T>
+cudaError_t set_local_smem(orqa_ctx* ctx) {
+    ctx->local_smem = sizeof(LocalSmem<W, T>);
+    cudaError_t e = cudaFuncSetAttribute(k_bucket_local<W, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ctx->local_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bucket_local<W, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ctx->local_smem);
+}
+
+}  // namespace
+
+extern "C" {
+
 uint64_t orqa_workspace_bytes_batch(int32_t n_qubits, int64_t capacity, int32_t n_problems) {
     if (n_qubits < 1 || n_qubits > 128 || capacity < 1 || capacity > 0x7fffffffLL || n_problems < 0 ||
         n_problems > ORQA_MAX_PROBLEMS)
@@ -1241,23 +1265,14 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
         return ORQA_EINVAL;
     }
     cudaError_t fe;
-    if (ctx->W == 1 && !ctx->fp32) {
-        ctx->local_smem = sizeof(LocalSmem<1, double>);
-        fe = cudaFuncSetAttribute(k_bucket_local<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)ctx->local_smem);
-    } else if (ctx->W == 1) {
-        ctx->local_smem = sizeof(LocalSmem<1, float>);
-        fe = cudaFuncSetAttribute(k_bucket_local<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)ctx->local_smem);
-    } else if (!ctx->fp32) {
-        ctx->local_smem = sizeof(LocalSmem<2, double>);
-        fe = cudaFuncSetAttribute(k_bucket_local<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)ctx->local_smem);
-    } else {
-        ctx->local_smem = sizeof(LocalSmem<2, float>);
-        fe = cudaFuncSetAttribute(k_bucket_local<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)ctx->local_smem);
-    }
+    if (ctx->W == 1 && !ctx->fp32)
+        fe = set_local_smem<1, double>(ctx);
+    else if (ctx->W == 1)
+        fe = set_local_smem<1, float>(ctx);
+    else if (!ctx->fp32)
+        fe = set_local_smem<2, double>(ctx);
+    else
+        fe = set_local_smem<2, float>(ctx);
     // the empty operator, committed in buffer 0
     if (fe != cudaSuccess || cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {

@@ -438,15 +438,14 @@ __device__ __forceinline__ long long warp_append(bool pred, unsigned long long* 
 }
 
 // Sum of a 64-bit value over a full warp (every lane calls it; all lanes
-// receive the total).  Used for event counters that may exceed 2^32.
+// receive the total), exact for per-lane values below 2^59: the low 16,
+// middle 16 and high 32 bits are summed separately in 32 bits (at most
+// 32 * (2^16 - 1) and 32 * 2^27), so a warp's total may exceed 2^32.
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        const unsigned lo = __shfl_xor_sync(FULL_MASK, (unsigned)v, d);
-        const unsigned hi = __shfl_xor_sync(FULL_MASK, (unsigned)(v >> 32), d);
-        v += ((unsigned long long)hi << 32) | lo;
-    }
-    return v;
+    const unsigned lo = __reduce_add_sync(FULL_MASK, (unsigned)(v & 0xffffu));
+    const unsigned mid = __reduce_add_sync(FULL_MASK, (unsigned)((v >> 16) & 0xffffu));
+    const unsigned hi = __reduce_add_sync(FULL_MASK, (unsigned)(v >> 32));
+    return (unsigned long long)lo + ((unsigned long long)mid << 16) + ((unsigned long long)hi << 32);
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v) {

@@ -494,6 +494,7 @@ struct LocalSmem {
     uint8_t s_idx[LB_MAX];
     int blk_delta[MAX_QUBITS];
     int warp_tot[33];
+    double drop_sq[LB_WARPS];   // per warp: sum of c^2 dropped (norm tracking only)
     int group_cursor;           // next unit group a warp claims
     SubRange cur, nx;           // the sub-range in work and the next one
     int n_units;
@@ -597,8 +598,9 @@ __device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int3
 // balance across CTAs.  The number of ranges J = ceil(total / range_target)
 // and the pass index are read from the device.  A sub-range holds at most
 // sub_max <= LB_MAX strings (the load of the shared-memory hash table is at
-// most sub_max / LB_TABLE).
-template <int W, typename T>
+// most sub_max / LB_TABLE).  TRACK adds up the c^2 of the dropped strings
+// (the norm bookkeeping); the timed path is compiled without it.
+template <int W, typename T, bool TRACK>
 __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const void* bk, const uint32_t* __restrict__ offsets, const int32_t* __restrict__ range_start,
     long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
@@ -616,9 +618,12 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         S.blk_delta[t] = 0;
         S.srot[t] = Coef<T>::rot(run, 0u, t);  // one read of the parameter table per qubit
     }
-    unsigned long long my_branch = 0, my_drop = 0, my_one = 0, my_two = 0;
-    double my_drop_sq = 0.0;
-    const bool track = run.track_norm != 0;
+    // per-lane event counts stay far below 2^32 (a launch handles at most
+    // 5 entries per string of the capacity, < 2^31, spread over every lane of
+    // the grid); the warp totals are summed in 64 bits
+    unsigned my_branch = 0, my_drop = 0;
+    unsigned long long my_one = 0, my_two = 0;
+    if (TRACK && tid < LB_WARPS) S.drop_sq[tid] = 0.0;
     // The work items are sub-ranges; the next one (claiming a new range when
     // the current range is done) is prepared by warp LB_WARPS - 1 while the
     // other warps work on the current one's units, so the latency of the
@@ -831,10 +836,12 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 T na, nb;
                 pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
-                my_drop += (unsigned long long)(!ka) + (unsigned long long)(!kb);
-                if (track) {  // block-uniform: the invariant check of the norm bookkeeping
-                    const double da = ka ? 0.0 : (double)na, db = kb ? 0.0 : (double)nb;
-                    my_drop_sq = fma(da, da, fma(db, db, my_drop_sq));
+                my_drop += (unsigned)(!ka) + (unsigned)(!kb);
+                if constexpr (TRACK) {
+                    if (!(ka && kb)) {
+                        const double da = ka ? 0.0 : (double)na, db = kb ? 0.0 : (double)nb;
+                        atomicAdd(&S.drop_sq[wp], fma(da, da, db * db));
+                    }
                 }
                 S.dense[ur][la] = na;
                 S.dense[ur][lb] = nb;
@@ -847,7 +854,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             __syncwarp();
             if (act) {
                 const int d = __popc(S.occ[ub + lane]) - pop_before;
-                my_branch += (unsigned long long)pop_before;
+                my_branch += (unsigned)pop_before;
                 if (d) atomicAdd(&S.blk_delta[pos[j]], d);
             }
         }
@@ -936,13 +943,12 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     }
     const unsigned long long nb = warp_sum64(my_branch);
     const unsigned long long nd = warp_sum64(my_drop);
-    const double nsq = track ? warp_sum_f64(my_drop_sq) : 0.0;
     if (lane == 0 && (nb | nd)) {
         atomicAdd(&ctr->branch_events, nb);
         atomicAdd(&ctr->dropped, nd);
         atomicAdd(&ctr->pairs_one, my_one);
         atomicAdd(&ctr->pairs_two, my_two);
-        if (track) atomicAdd(&ctr->dropped_sq, nsq);
+        if (TRACK) atomicAdd(&ctr->dropped_sq, S.drop_sq[wp]);
     }
     __syncthreads();
     for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)
