@@ -399,6 +399,96 @@ __device__ __forceinline__ int chunk_positions2(const uint64_t (&f)[W], int skip
     return r < CHUNK_BITS ? r : CHUNK_BITS;
 }
 
+// chunk_positions2 with the first chunk's positions packed 7 bits each
+// (position j at bits 7j .. 7j + 6; returns their count) and the second
+// chunk as a bit mask m2 with np2 bits: registers only, no indexed arrays.
+template <int W>
+__device__ __forceinline__ int chunk_positions2_packed(const uint64_t (&f)[W], int skip, uint64_t& packed,
+                                                       uint64_t (&m2)[W], int& np2) {
+    int r = 0;
+    packed = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) m2[w] = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t v = f[w];
+        if (r == 2 * CHUNK_BITS) break;
+        const int cnt = __popcll(v);
+        if (skip >= cnt) {
+            skip -= cnt;
+            continue;
+        }
+        if (skip > 0) {
+            v &= ~((1ull << nth_set_bit(v, skip)) - 1ull);
+            skip = 0;
+        }
+        while (v != 0 && r < 2 * CHUNK_BITS) {
+            const int b = __ffsll((long long)v) - 1;
+            if (r < CHUNK_BITS)
+                packed |= (uint64_t)(64 * w + b) << (7 * r);
+            else
+                m2[w] |= 1ull << b;
+            ++r;
+            v &= v - 1;
+        }
+    }
+    np2 = r > CHUNK_BITS ? r - CHUNK_BITS : 0;
+    return r < CHUNK_BITS ? r : CHUNK_BITS;
+}
+
+__device__ __forceinline__ int packed_pos(uint64_t packed, int j) { return (int)((packed >> (7 * j)) & 127u); }
+
+// Mask m of the set bits of f whose rank among the set bits is in
+// [skip, skip + CHUNK_BITS) (the chunk of one pass); returns their count.
+template <int W>
+__device__ __forceinline__ int chunk_mask(const uint64_t (&f)[W], int skip, uint64_t (&m)[W]) {
+    int r = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        m[w] = 0;
+        uint64_t v = f[w];
+        const int cnt = __popcll(v);
+        if (r == CHUNK_BITS || skip >= cnt) {
+            skip = r == CHUNK_BITS ? skip : skip - cnt;
+            continue;
+        }
+        if (skip > 0) {
+            v &= ~((1ull << nth_set_bit(v, skip)) - 1ull);
+            skip = 0;
+        }
+        // the lowest CHUNK_BITS - r set bits of v
+        const int take = min(__popcll(v), CHUNK_BITS - r);
+        const uint64_t above = take < __popcll(v) ? ~((1ull << nth_set_bit(v, take)) - 1ull) : 0ull;
+        m[w] = v & ~above;
+        r += take;
+    }
+    return r;
+}
+
+// The bits of x at the positions of mask m, in ascending order (a unit slot).
+template <int W>
+__device__ __forceinline__ int gather_bits(const uint64_t (&x)[W], const uint64_t (&m)[W]) {
+    int idx = 0, j = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        for (uint64_t v = m[w]; v; v &= v - 1, ++j) idx |= (int)((x[w] >> (__ffsll((long long)v) - 1)) & 1ull) << j;
+    return idx;
+}
+
+// Hash of a string's unit key for chunk pass `pass` (z, and x with the
+// chunk's bits cleared; see unit_key_hash), from the chunk mask only.
+template <int W>
+__device__ __forceinline__ uint64_t unit_hash(const uint64_t (&x)[W], const uint64_t (&z)[W], const uint64_t* mask,
+                                              int pass, unsigned pid) {
+    uint64_t f[W], m[W], xb[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) f[w] = z[w] & mask[w];
+    chunk_mask<W>(f, CHUNK_BITS * pass, m);
+#pragma unroll
+    for (int w = 0; w < W; ++w) xb[w] = x[w] & ~m[w];
+    return with_pid(hash_key<W>(z, xb, pid), pid);
+}
+
 // Unit key of a string for chunk pass `pass` of an X-rotation run: z and x
 // with the chunk's bits cleared (see the unit definition in the layer
 // kernels).  Returns its 64-bit hash; fills the chunk's qubit positions,
@@ -560,6 +650,21 @@ __device__ __forceinline__ void pair_entry(const Rot<double>& r, double u1, doub
         na = y_side ? Coef<double>::negate(q) : p;
         nb = y_side ? p : q;
     }
+}
+
+// A pair with one member present, u its coefficient: exactly the one-member
+// case of pair_entry (cos u, sin u at sigma_z; -sin u, cos u at sigma_y).
+__device__ __forceinline__ void lone_entry(const Rot<double>& r, double u, bool y_side, double& na, double& nb) {
+    const double p = __dmul_rn(r.c, u), q = __dmul_rn(r.s, u);
+    na = y_side ? Coef<double>::negate(q) : p;
+    nb = y_side ? p : q;
+}
+
+__device__ __forceinline__ void lone_entry(const Rot<float>& r, float u, bool y_side, float& na, float& nb) {
+    float p, q;
+    one_member(r, u, p, q);
+    na = y_side ? Coef<float>::negate(q) : p;
+    nb = y_side ? p : q;
 }
 
 __device__ __forceinline__ void pair_entry(const Rot<float>& r, float u1, float u2, bool two, bool y_side,

@@ -185,9 +185,7 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
                 atomicOr(&ctr->err, ERR_OVERFLOW);
             }
             if (act) {
-                int pos[CHUNK_BITS], np, idx;
-                bool more;
-                const uint64_t h = unit_key_hash<W>(x, z[k], run.mask, 0, pos, np, idx, more, pid);
+                const uint64_t h = unit_hash<W>(x, z[k], run.mask, 0, pid);
                 const int rk = bucket_rank(fcount, fine_bucket(h, fshift), ctr);
                 if (slot < cap) {
                     active.h[slot] = h;
@@ -653,14 +651,11 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         load_record<W, T>(bk, s0 + i, x, z, c, h);
 #pragma unroll
         for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
-        int pos[CHUNK_BITS];
-        bool more;
-        const int np = chunk_positions<W>(f, CHUNK_BITS * pass, pos, more);
-        int idx = 0;
-        for (int j = 0; j < np; ++j) {
-            idx |= bit_of<W>(x, pos[j]) << j;
-            clear_bit<W>(x, pos[j]);
-        }
+        uint64_t m[W];
+        chunk_mask<W>(f, CHUNK_BITS * pass, m);
+        const int idx = gather_bits<W>(x, m);
+#pragma unroll
+        for (int w = 0; w < W; ++w) x[w] &= ~m[w];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             S.sx[w][i] = x[w];
@@ -760,8 +755,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         const int u = g + lane;
         const bool own = lane < LB_UPW && u < n_units;
         uint64_t z[W], xb[W], xn[W];
-        int pos[CHUNK_BITS] = {0, 0, 0, 0, 0}, pos2[CHUNK_BITS] = {0, 0, 0, 0, 0};
-        int np = 0, np2 = 0;
+        uint64_t ppos = 0;  // this pass's chunk positions, 7 bits each (packed_pos)
+        int np = 0;
         bool more = false;
         unsigned upid = 0;
 #pragma unroll
@@ -769,17 +764,20 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         if (own) {
             const int rep = S.u_rep[u];
             upid = S.spid[rep];
-            uint64_t f[W];
+            uint64_t f[W], m2[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 z[w] = S.sz[w][rep];
                 xb[w] = S.sx[w][rep];
-                xn[w] = xb[w];
                 f[w] = z[w] & run.mask[w];
             }
-            np = chunk_positions2<W>(f, CHUNK_BITS * pass, pos, pos2, np2);
+            int np2 = 0;
+            np = chunk_positions2_packed<W>(f, CHUNK_BITS * pass, ppos, m2, np2);
             more = np2 > 0;
-            for (int j = 0; j < np2; ++j) clear_bit<W>(xn, pos2[j]);
+            // the next pass's key: x outside the next chunk (this chunk's bits
+            // are set per output string below; the two chunks are disjoint)
+#pragma unroll
+            for (int w = 0; w < W; ++w) xn[w] = xb[w] & ~m2[w];
         }
         if (lane < LB_UPW) S.occ[ub + lane] = own ? uocc[u] : 0u;
         // strings of this warp's units into their slots (a contiguous run of
@@ -806,7 +804,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 sgl = lo ^ hi;
                 dbl = lo & hi;
                 pop_before = __popc(o);
-                S.hrot[ub + lane] = batched ? Coef<T>::rot(run, upid, pos[j]) : S.srot[pos[j]];
+                const int qj = packed_pos(ppos, j);
+                S.hrot[ub + lane] = batched ? Coef<T>::rot(run, upid, qj) : S.srot[qj];
             }
             unsigned tot;
             unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
@@ -825,16 +824,22 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 o2 += d ? 1u : 0u;
             }
             __syncwarp();
-            for (unsigned t = lane; t < n1 + n2; t += 32) {
+            for (unsigned t0 = 0; t0 < n1 + n2; t0 += 32) {  // warp-uniform
+                const unsigned t = t0 + lane;
+                if (t >= n1 + n2) continue;
                 const bool two = t >= n1;
                 const int e = S.list[wp][t];
                 const int ur = ub + (e >> 6), la = e & 31;
                 const bool y_side = (e & 32) != 0;
                 const int lb = la | bit;
                 const T u1 = S.dense[ur][y_side ? lb : la];
-                const T u2 = two ? S.dense[ur][lb] : u1;
                 T na, nb;
-                pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
+                if (t0 + 32 <= n1) {  // warp-uniform: one-member entries only (2 products)
+                    lone_entry(S.hrot[ur], u1, y_side, na, nb);
+                } else {
+                    const T u2 = two ? S.dense[ur][lb] : u1;
+                    pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
+                }
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned)(!ka) + (unsigned)(!kb);
                 if constexpr (TRACK) {
@@ -855,7 +860,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             if (act) {
                 const int d = __popc(S.occ[ub + lane]) - pop_before;
                 my_branch += (unsigned)pop_before;
-                if (d) atomicAdd(&S.blk_delta[pos[j]], d);
+                if (d) atomicAdd(&S.blk_delta[packed_pos(ppos, j)], d);
             }
         }
         // ---- outputs: flattened over the warp, one reservation per warp and list
@@ -892,7 +897,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             const unsigned dof = __shfl_sync(FULL_MASK, doff, L);
             const unsigned nof = __shfl_sync(FULL_MASK, noff, L);
             const int npl = __shfl_sync(FULL_MASK, np, L);
-            const int np2l = __shfl_sync(FULL_MASK, np2, L);
+            const uint64_t pp = shfl64(ppos, L);
             const unsigned ppl = __shfl_sync(FULL_MASK, upid, L);
             uint64_t x[W], zz[W], x2[W];
 #pragma unroll
@@ -901,29 +906,20 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 zz[w] = shfl64(z[w], L);
                 x2[w] = shfl64(xn[w], L);
             }
-            int pl[CHUNK_BITS], p2l[CHUNK_BITS];
-#pragma unroll
-            for (int j = 0; j < CHUNK_BITS; ++j) {
-                pl[j] = __shfl_sync(FULL_MASK, pos[j], L);
-                p2l[j] = __shfl_sync(FULL_MASK, pos2[j], L);
-            }
             if (k >= wtot) continue;
             const int r = (int)(k - fl);
             const int l = nth_set_bit32(oc, r);
-            for (int j = 0; j < npl; ++j)
-                if ((l >> j) & 1) {
-                    set_bit<W>(x, pl[j]);
-                    set_bit<W>(x2, pl[j]);
+#pragma unroll
+            for (int j = 0; j < CHUNK_BITS; ++j)
+                if (j < npl && ((l >> j) & 1)) {
+                    const int q = packed_pos(pp, j);
+                    set_bit<W>(x, q);
+                    set_bit<W>(x2, q);
                 }
             const long long slot = (long long)(mr ? base_next + nof + r : base_done + dof + r);
             StrList dst = mr ? next : done;
             uint64_t h = 0;
-            if (mr) {
-                // the next pass's chunk bits are cleared in its key (some of them
-                // may be this pass's bits just set)
-                for (int j = 0; j < np2l; ++j) clear_bit<W>(x2, p2l[j]);
-                h = with_pid(hash_key<W>(zz, x2, ppl), ppl);
-            }
+            if (mr) h = with_pid(hash_key<W>(zz, x2, ppl), ppl);  // x2: x outside the next chunk
             const int rk = mr ? bucket_rank(fcount_next, fine_bucket(h, fshift), ctr) : 0;
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
