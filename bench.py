@@ -55,6 +55,8 @@ def parse_args(argv=None):
                     help="sweep workloads: pick the launch tuning by measurement before warm-up")
     ap.add_argument("--compare-plain", action="store_true",
                     help="sweep workloads: also time the plain FP64 path, one problem after another")
+    ap.add_argument("--truncation", default="absolute", choices=["absolute", "relative"],
+                    help="relative: |c| <= delta * max|c| after every X gate (Eq. truncation1), gate by gate")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed evolutions: no norm invariants, delta sequence, end-to-end run or "
                          "sweep comparison (for profiler runs)")
@@ -142,13 +144,13 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def make_gpu_runner(wl, capacity, profile=True, fp32=False):
+def make_gpu_runner(wl, capacity, profile=True, fp32=False, relative=False):
     import numpy as np
     import torch
     from paper_2506_13241_gb300 import orqa as B
 
     n = wl["n"]
-    ctx = B.Context(n, capacity, profile=profile, fp32=fp32)
+    ctx = B.Context(n, capacity, profile=profile, fp32=fp32, relative=relative)
     layers = [B.gate_array(layer) for layer in wl["layers"]]
     x_h, z_h = B.strings_from_labels([lab for lab, _ in wl["observable"]], n)
     c_h = np.array([c for _, c in wl["observable"]], dtype=np.float64)
@@ -229,7 +231,8 @@ def run_gpu(args, wl, rank, world):
     torch.cuda.set_device(local)
     capacity = int(args.capacity) if args.capacity else default_capacity(wl)
     ctx, step_dev, step_host, h2d, d2h, fp64, step_inv = make_gpu_runner(wl, capacity,
-                                                                         fp32=(args.precision == "fp32"))
+                                                                         fp32=(args.precision == "fp32"),
+                                                                         relative=(args.truncation == "relative"))
     stream = ctx.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -240,7 +243,7 @@ def run_gpu(args, wl, rank, world):
 
     invariants = None
     for k in range(args.warmup):
-        if k == 0 and not args.no_extras and wl["delta"] > 0:
+        if k == 0 and not args.no_extras and wl["delta"] > 0 and args.truncation == "absolute":
             invariants = step_inv()  # the first warm-up evolution checks the norm bookkeeping
         else:
             step_dev()
@@ -281,7 +284,7 @@ def run_gpu(args, wl, rank, world):
         e2e_s += time.perf_counter() - t0
         e2e_updates += upd
     deltas = None
-    if not args.no_extras and wl["delta"] > 0:
+    if not args.no_extras and wl["delta"] > 0 and args.truncation == "absolute":
         deltas = delta_sequence(wl, mags, step_dev)
     times, sums = reduce_over_ranks([total_ms, e2e_s], [total_updates, e2e_updates], "cuda")
     return dict(total_ms=times[0], updates=sums[0], mags=mags, peak=peak, clocks=clk,
@@ -407,7 +410,7 @@ def roofline_entry(prof, steps, workload=None, precision="fp64", n_qubits=127):
 ORACLE_MAX_TERMS = 20_000_000  # keeps the std::map oracle within a few GB of host memory
 
 
-def oracle_sample(wl, seconds: float):
+def oracle_sample(wl, seconds: float, relative: bool = False):
     """Runs the oracle on the workload from its start, gate by gate, and stops
     after the gate that passes ``seconds`` (or when the operator outgrows
     ORACLE_MAX_TERMS), so the sample is bounded whatever the workload size.
@@ -428,7 +431,10 @@ def oracle_sample(wl, seconds: float):
                 if time.perf_counter() - t0 >= seconds or size > ORACLE_MAX_TERMS:
                     return updates, time.perf_counter() - t0, steps, partial, mags
                 updates += size
-                op.apply(g, wl["delta"])
+                if relative:
+                    op.apply_rel(g, wl["delta"])
+                else:
+                    op.apply(g, wl["delta"])
                 partial += 1
         mags.append(op.expect_zero())
         steps = t + 1
@@ -453,8 +459,8 @@ def host_cpu():
     return {"model": model or platform.machine(), "nproc": os.cpu_count()}
 
 
-def cpu_baseline(wl, seconds):
-    upd, secs, steps, partial, mags = oracle_sample(wl, seconds)
+def cpu_baseline(wl, seconds, relative=False):
+    upd, secs, steps, partial, mags = oracle_sample(wl, seconds, relative)
     return {"value": upd / secs if secs > 0 else None, "unit": UNIT, "cores": 1, "kind": "oracle",
             "host": host_cpu(),
             "sample": "first %d of %d time steps of %s plus %d gates of the next (%d string-gate "
@@ -507,11 +513,13 @@ def error_entry(mags, ref):
     return {"steps_compared": k, "max_abs": max(per_step) if per_step else None, "per_step": per_step}
 
 
-def workload_config(wl, precision="fp64"):
+def workload_config(wl, precision="fp64", truncation="absolute"):
     return {"workload": wl["name"], "lattice": "heavy-hex 127" if wl["n"] == 127 else "chain %d" % wl["n"],
             "n_qubits": wl["n"], "theta_x": wl["theta_x"], "theta_zz": W.THETA_ZZ,
             "observable": "Z_62" if wl["n"] == 127 else "Z_6", "time_steps": wl["steps"],
-            "delta": wl["delta"], "truncation": "absolute |c| < delta after every X gate",
+            "delta": wl["delta"],
+            "truncation": ("absolute |c| < delta after every X gate" if truncation == "absolute" else
+                           "relative |c| <= delta * max|c| after every X gate, one gate per pass"),
             "coefficients": precision, "l2": "flushed between timed steps"}
 
 
@@ -839,7 +847,7 @@ def main(argv=None):
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
-            "data": "synthetic", "config": workload_config(wl, args.precision),
+            "data": "synthetic", "config": workload_config(wl, args.precision, args.truncation),
             "roofline": roofline_entry(res["prof"], args.steps, wl["name"], args.precision, wl["n"]),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
@@ -857,11 +865,12 @@ def main(argv=None):
         # The precision form's error per step against the GPU FP64 path on
         # the same workload (one untimed evolution after the timed run).
         line["magnetization_error_vs_gpu_fp64"] = error_entry(res["mags"], fp64_magnetization(wl, res["capacity"]))
-    if not args.no_extras and world == 1 and wl["n"] == 127 and args.precision == "fp64":
+    if not args.no_extras and world == 1 and wl["n"] == 127 and args.precision == "fp64" and \
+            args.truncation == "absolute":
         res["prof"] = None
         line["sweep"] = sweep_comparison()
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is an N = 1 figure
-        cb = cpu_baseline(wl, args.cpu_seconds)
+        cb = cpu_baseline(wl, args.cpu_seconds, args.truncation == "relative")
         om = cb.pop("magnetization")
         line["magnetization_error_vs_oracle"] = error_entry(res["mags"], om)
         line["cpu_baseline"] = cb

@@ -339,11 +339,13 @@ orqa_status orqa_run_program(orqa_ctx* ctx, const orqa_layer_desc* layers, int32
  * result; they trade occupancy, scatter locality and shared-memory hash
  * load.
  *   range_target   strings per unit-kernel CTA range (tile), 128..4096
- *   sub_max        most strings one shared-memory sub-range holds, 256..512;
- *                  the shared hash table has 1024 slots, so its load is at
- *                  most sub_max / 1024
- *   bucket_density strings per fine bucket at full capacity (8, 16 or 32): the
- *                  number of hash bits that partition the strings
+ *   sub_max        most strings one shared-memory sub-range holds, 128..256;
+ *                  the shared hash table has 512 slots, so its load is at
+ *                  most sub_max / 512
+ *   bucket_density strings per fine bucket at full capacity (8, 16, 32, 64 or
+ *                  128, at most sub_max / 4: a bucket must fit one sub-range
+ *                  with margin): the number of hash bits that partition the
+ *                  strings
  *   grid_per_sm    CTAs per SM of the streaming kernels, 1..32 */
 typedef struct {
     int32_t range_target;
