@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(uint32_t* offsets, co
 // W = 2, exactly 32 bytes for W = 1 -- so the scattered writes never leave a
 // partly written sector.
 // ---------------------------------------------------------------------------
-constexpr int SCATTER_ILP = 8;
+constexpr int SCATTER_ILP = 4;
 
 template <int W, typename T>
 __device__ __forceinline__ void store_record(void* base, long long i, const uint64_t (&x)[W],
@@ -392,16 +392,25 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
     for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x;
          base - threadIdx.x < n; base += stride) {  // warp-uniform: all lanes iterate together
+        // every load of the batch is issued before the first store, so the
+        // warp waits for memory once per batch, not once per string
         long long slot[SCATTER_ILP];
-        uint64_t h[SCATTER_ILP];
+        uint64_t h[SCATTER_ILP], xs[SCATTER_ILP][W], zs[SCATTER_ILP][W];
+        T cs[SCATTER_ILP];
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
             h[k] = 0;
             slot[k] = -1;
+            cs[k] = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) xs[k][w] = zs[k][w] = 0;
             if (i < n) {
                 h[k] = src.h[i];
                 slot[k] = src.rank[i];
+                load_plane<W>(src.x, i, xs[k]);
+                load_plane<W>(src.z, i, zs[k]);
+                cs[k] = reinterpret_cast<const T*>(src.c)[i];
             }
         }
 #pragma unroll
@@ -409,17 +418,15 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
             if (slot[k] >= 0) slot[k] += (long long)offsets[fine_bucket(h[k], fshift)];
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
-            const long long i = base + (long long)k * blockDim.x;
             long long sl = slot[k];
             if (sl >= cap) {  // only reachable after an undetected count error; never write past the records
                 atomicOr(&ctr->err, ERR_OVERFLOW);
                 sl = -1;
             }
             if (sl >= 0) {
-                uint64_t x[W], z[W];
-                load_plane<W>(src.x, i, x);
-                load_plane<W>(src.z, i, z);
-                const T c = reinterpret_cast<const T*>(src.c)[i];
+                const uint64_t (&x)[W] = xs[k];
+                const uint64_t (&z)[W] = zs[k];
+                const T c = cs[k];
                 if constexpr (W == 2) {
                     stage[wp][lane][0] = make_uint4((unsigned)x[0], (unsigned)(x[0] >> 32), (unsigned)x[1],
                                                     (unsigned)(x[1] >> 32));
@@ -481,7 +488,7 @@ struct LocalSmem {
     uint64_t sx[W][LB_MAX];     // x with the chunk bits cleared
     uint64_t sz[W][LB_MAX];
     T sc[LB_MAX];
-    T dense[LB_RU][32];         // unit rows (slot = chunk bits)
+    T dense[LB_RU][32];         // unit rows: slot l of row r at column dcol(r, l)
     alignas(4) uint16_t table[LB_TABLE];  // hash table of string indices (0xffff: empty), then unit masks
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
@@ -502,6 +509,11 @@ struct LocalSmem {
     SubRange cur, nx;           // the sub-range in work and the next one
     int n_units;
 };
+
+// Column of slot l in dense row r: the slot XOR the row's low bits, so that
+// the same slot of different rows (the common case in a level's pair list)
+// falls in different shared-memory banks.
+__device__ __forceinline__ int dcol(int r, int l) { return l ^ (r & 15); }
 
 __device__ __forceinline__ unsigned level_mask(int j) {
     // slots whose bit j is clear
@@ -799,7 +811,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             const int k_lo = S.ustart[g], k_hi = S.ustart[min(g + LB_UPW, n_units)];
             for (int k = k_lo + lane; k < k_hi; k += 32) {
                 const int i = S.s_order[k];
-                S.dense[ub + S.s_unit[i] - g][S.s_idx[i]] = S.sc[i];
+                const int r = ub + S.s_unit[i] - g;
+                S.dense[r][dcol(r, S.s_idx[i])] = S.sc[i];
             }
         }
         __syncwarp();
@@ -845,12 +858,12 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 const int ur = ub + (e >> 6), la = e & 31;
                 const bool y_side = (e & 32) != 0;
                 const int lb = la | bit;
-                const T u1 = S.dense[ur][y_side ? lb : la];
+                const T u1 = S.dense[ur][dcol(ur, y_side ? lb : la)];
                 T na, nb;
                 if (t0 + 32 <= n1) {  // warp-uniform: one-member entries only (2 products)
                     lone_entry(S.hrot[ur], u1, y_side, na, nb);
                 } else {
-                    const T u2 = two ? S.dense[ur][lb] : u1;
+                    const T u2 = two ? S.dense[ur][dcol(ur, lb)] : u1;
                     pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
                 }
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
@@ -861,8 +874,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                         atomicAdd(&S.drop_sq[wp], fma(da, da, db * db));
                     }
                 }
-                S.dense[ur][la] = na;
-                S.dense[ur][lb] = nb;
+                S.dense[ur][dcol(ur, la)] = na;
+                S.dense[ur][dcol(ur, lb)] = nb;
                 // occupancy of the pair before (both, or the present member) and after
                 const unsigned was = two ? ((1u << la) | (1u << lb)) : (1u << (y_side ? lb : la));
                 const unsigned now = (ka ? (1u << la) : 0u) | (kb ? (1u << lb) : 0u);
@@ -937,7 +950,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, zz);
-                reinterpret_cast<T*>(dst.c)[slot] = S.dense[ub + L][l];
+                reinterpret_cast<T*>(dst.c)[slot] = S.dense[ub + L][dcol(ub + L, l)];
                 if (dst.pid) dst.pid[slot] = (uint16_t)ppl;
                 if (mr) {
                     dst.h[slot] = h;
