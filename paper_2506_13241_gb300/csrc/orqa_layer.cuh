@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(uint32_t* offsets, co
 // W = 2, exactly 32 bytes for W = 1 -- so the scattered writes never leave a
 // partly written sector.
 // ---------------------------------------------------------------------------
-constexpr int SCATTER_ILP = 4;
+constexpr int SCATTER_ILP = 8;
 
 template <int W, typename T>
 __device__ __forceinline__ void store_record(void* base, long long i, const uint64_t (&x)[W],
@@ -392,25 +392,16 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
     const long long stride = (long long)gridDim.x * blockDim.x * SCATTER_ILP;
     for (long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ILP + threadIdx.x;
          base - threadIdx.x < n; base += stride) {  // warp-uniform: all lanes iterate together
-        // every load of the batch is issued before the first store, so the
-        // warp waits for memory once per batch, not once per string
         long long slot[SCATTER_ILP];
-        uint64_t h[SCATTER_ILP], xs[SCATTER_ILP][W], zs[SCATTER_ILP][W];
-        T cs[SCATTER_ILP];
+        uint64_t h[SCATTER_ILP];
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
             const long long i = base + (long long)k * blockDim.x;
             h[k] = 0;
             slot[k] = -1;
-            cs[k] = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w) xs[k][w] = zs[k][w] = 0;
             if (i < n) {
                 h[k] = src.h[i];
                 slot[k] = src.rank[i];
-                load_plane<W>(src.x, i, xs[k]);
-                load_plane<W>(src.z, i, zs[k]);
-                cs[k] = reinterpret_cast<const T*>(src.c)[i];
             }
         }
 #pragma unroll
@@ -418,15 +409,17 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(StrList src, long long c
             if (slot[k] >= 0) slot[k] += (long long)offsets[fine_bucket(h[k], fshift)];
 #pragma unroll
         for (int k = 0; k < SCATTER_ILP; ++k) {
+            const long long i = base + (long long)k * blockDim.x;
             long long sl = slot[k];
             if (sl >= cap) {  // only reachable after an undetected count error; never write past the records
                 atomicOr(&ctr->err, ERR_OVERFLOW);
                 sl = -1;
             }
             if (sl >= 0) {
-                const uint64_t (&x)[W] = xs[k];
-                const uint64_t (&z)[W] = zs[k];
-                const T c = cs[k];
+                uint64_t x[W], z[W];
+                load_plane<W>(src.x, i, x);
+                load_plane<W>(src.z, i, z);
+                const T c = reinterpret_cast<const T*>(src.c)[i];
                 if constexpr (W == 2) {
                     stage[wp][lane][0] = make_uint4((unsigned)x[0], (unsigned)(x[0] >> 32), (unsigned)x[1],
                                                     (unsigned)(x[1] >> 32));
