@@ -501,7 +501,7 @@ def fp64_magnetization(wl, capacity):
     import torch
     gc.collect()
     torch.cuda.empty_cache()
-    _, step_dev, _, _, _, _ = make_gpu_runner(wl, capacity, profile=False, fp32=False)
+    step_dev = make_gpu_runner(wl, capacity, profile=False, fp32=False)[1]
     _, mags, _ = step_dev()
     return mags
 
