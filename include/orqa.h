@@ -176,7 +176,10 @@ orqa_status orqa_set_operator_device(orqa_ctx* ctx, int64_t n, const uint64_t* x
  * one gate at a time as in Algorithm 1).  All gates must be of one kind.
  *   ORQA_RZZ (Clifford): each string maps to exactly one string with an
  *     exact sign; nothing merges and |c| is unchanged.  Strings with
- *     |c| < delta are then dropped.
+ *     |c| < delta are then dropped.  The library may hold such a layer
+ *     back and apply it inside the next ORQA_RX layer's first pass over the
+ *     operator, which saves a pass; every other call that reads or changes
+ *     the operator applies it first, so no result differs.
  *   ORQA_RX: after every gate, duplicates are merged and strings with
  *     c == 0 or |c| < delta are dropped (the truncation loop of Algorithm 1
  *     with the absolute threshold); the result is the one of that per-gate
@@ -426,13 +429,19 @@ orqa_status orqa_shard_append(orqa_ctx* ctx, int64_t n, const uint64_t* recv);
  *                                 default up to 63 (fewer, fuller buckets:
  *                                 one above the shared-memory range size
  *                                 returns ORQA_ECAPACITY); orqa_set_tuning
- *                                 restores the default */
+ *                                 restores the default
+ *   ORQA_DEBUG_NO_ZZ_FUSION       1: every ORQA_RZZ layer is applied by a
+ *                                 pass of its own at once, never held back
+ *                                 for the next X layer's entry split (the
+ *                                 results are the same bit for bit; the
+ *                                 tests compare the two) */
 enum {
     ORQA_DEBUG_SPIN_LIMIT = 1,
     ORQA_DEBUG_POISON_MERGE_TABLE = 2,
     ORQA_DEBUG_MERGE_TABLE_SLOTS = 3,
     ORQA_DEBUG_PASS_LIMIT = 4,
-    ORQA_DEBUG_BUCKET_SHIFT = 5
+    ORQA_DEBUG_BUCKET_SHIFT = 5,
+    ORQA_DEBUG_NO_ZZ_FUSION = 6
 };
 orqa_status orqa_debug_set(orqa_ctx* ctx, int32_t knob, int64_t value);
 

@@ -116,6 +116,14 @@ struct orqa_ctx {
     bool poison_table = false;
     long long dbg_table_slots = 0;
     int pass_limit = MAX_PASSES;
+    // A ZZ layer held back to be applied by the entry split of the next X
+    // layer (k_rx_split<.., ZZ = true>), which saves the layer's own pass
+    // over the operator.  Every other operation on the operator applies it
+    // first (settle_zz).  zz_fuse = false (orqa_debug_set) applies every ZZ
+    // layer at once.
+    bool zz_pending = false;
+    ZZGroups zz_pend{};
+    bool zz_fuse = true;
 
     // ORQA_FLAG_PROFILE: CUDA events around every launch, resolved at the
     // next stream synchronisation.
@@ -152,6 +160,9 @@ struct orqa_ctx {
 namespace {
 
 constexpr size_t ALIGN = 256;
+
+// The ZZ stage of an entry split that has none (the kernel never reads it).
+const ZZGroups kNoZZ{};
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -579,19 +590,48 @@ orqa_status truncate_abs(orqa_ctx* ctx, double delta, long long* dropped, double
     return ORQA_OK;
 }
 
+// Applies the ZZ layer G to the committed operator in place.
+template <int W, typename T>
+orqa_status launch_rzz(orqa_ctx* ctx, const ZZGroups& G) {
+    if (ctx->n == 0) return ORQA_OK;
+    // error bits that a failed earlier call left would make the kernel skip
+    if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
+    const double b = (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T));
+    const int r = prof_begin(ctx, K_RZZ, b);
+    k_rzz_layer<W, T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(ctx->buf[ctx->cur], ctx->cap, ctx->ctr, G);
+    prof_end(ctx, r);
+    prof_set_floor(ctx, r, b);
+    LAUNCH_CHECK(ctx);
+    return ORQA_OK;
+}
+
+template <int W, typename T>
+orqa_status settle_zz_t(orqa_ctx* ctx) {
+    const orqa_status st = launch_rzz<W, T>(ctx, ctx->zz_pend);
+    if (st == ORQA_OK) ctx->zz_pending = false;
+    return st;
+}
+
+// Applies a held-back ZZ layer, if any, to the committed operator.
+orqa_status settle_zz(orqa_ctx* ctx) {
+    return ctx->zz_pending ? ORQA_DISPATCH(ctx, settle_zz_t, ctx) : ORQA_OK;
+}
+
+// A ZZ layer of one launch is held back for the next X layer's entry split
+// (the operator it leaves is the same; an X layer that fails leaves it
+// held back over the unchanged operator).
 template <int W, typename T>
 orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     std::vector<ZZGroups> launches;
-    orqa_status bst = build_zz_groups(ctx, g, ng, launches);
-    if (bst != ORQA_OK) return bst;
-    StrList s = ctx->buf[ctx->cur];
-    for (const ZZGroups& l : launches) {
-        if (ctx->n == 0) break;
-        const int r = prof_begin(ctx, K_RZZ, (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T)));
-        k_rzz_layer<W, T><<<grid_for(ctx, ctx->n), 256, 0, ctx->stream>>>(s, ctx->cap, ctx->ctr, l);
-        prof_end(ctx, r);
-        prof_set_floor(ctx, r, (double)ctx->n * (string_bytes<W, T>() + 8.0 * W + sizeof(T)));
-        LAUNCH_CHECK(ctx);
+    orqa_status st = build_zz_groups(ctx, g, ng, launches);
+    if (st != ORQA_OK) return st;
+    if (ctx->zz_pending && (st = settle_zz_t<W, T>(ctx)) != ORQA_OK) return st;
+    if (ctx->zz_fuse && launches.size() == 1 && ctx->n > 0) {
+        ctx->zz_pend = launches[0];
+        ctx->zz_pending = true;
+    } else {
+        for (const ZZGroups& l : launches)
+            if ((st = launch_rzz<W, T>(ctx, l)) != ORQA_OK) return st;
     }
     ctx->stats.last_layer_in = ctx->n;
     ctx->stats.last_layer_peak = ctx->n;
@@ -602,10 +642,12 @@ orqa_status apply_rzz(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta) {
     ctx->stats.pair_updates_two = 0;
     ctx->stats.chunk_passes = 0;
     ctx->stats.dropped_sum_sq = 0.0;
+    // |c| is unchanged by the layer and strings map one to one, so the
+    // truncation may run before the held-back layer is applied
     if (delta > ctx->clean_delta && ctx->n > 0) {
         long long dropped = 0;
         double dsq = 0.0;
-        orqa_status st = truncate_abs<W, T>(ctx, delta, &dropped, &dsq);
+        st = truncate_abs<W, T>(ctx, delta, &dropped, &dsq);
         if (st != ORQA_OK) return st;
         ctx->stats.dropped = dropped;
         ctx->stats.dropped_sum_sq = dsq;
@@ -746,10 +788,15 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 2, ctx->stream));
     int r_split = -1;
+    const bool fused = ctx->zz_pending;  // a held-back ZZ layer is applied by the split
     if (n_in > 0) {
         r_split = prof_begin(ctx, K_SPLIT, 0);
-        k_rx_split<W, T><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(L.src, L.done, L.act, ctx->cap, run, ctx->ctr,
-                                                                     ctx->fcount, ctx->fshift);
+        if (fused)
+            k_rx_split<W, T, true><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(
+                L.src, L.done, L.act, ctx->cap, run, ctx->ctr, ctx->fcount, ctx->fshift, ctx->zz_pend);
+        else
+            k_rx_split<W, T, false><<<grid_for(ctx, n_in), 256, 0, ctx->stream>>>(
+                L.src, L.done, L.act, ctx->cap, run, ctx->ctr, ctx->fcount, ctx->fshift, kNoZZ);
         prof_end(ctx, r_split);
         LAUNCH_CHECK(ctx);
     }
@@ -757,8 +804,13 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     LAUNCH_CHECK(ctx);
     Counters h{};
     if ((st = sync_counters(ctx, &h)) != ORQA_OK) return st;
-    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + sizeof(T)) + (double)(h.n_done + h.n_active) * (8.0 * W + R) +
+    // z and c of every string, x of every routed one (of every string when
+    // fused), the routed string written, hash and rank of the active ones
+    prof_set_bytes(ctx, r_split, (double)n_in * (8.0 * W + sizeof(T) + (fused ? 8.0 * W : 0.0)) +
+                                     (double)(h.n_done + h.n_active) * ((fused ? 0.0 : 8.0 * W) + R) +
                                      (double)h.n_active * 12.0);
+    // the fused ZZ layer's floor (R read, z and c written per string)
+    if (fused) prof_set_floor(ctx, r_split, (double)n_in * (R + 8.0 * W + sizeof(T)));
     prof_resolve(ctx);
     if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
     int pass = 0;
@@ -801,6 +853,7 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
         if (k == 0) pop -= (long long)h.split_dropped;
     }
     if ((st = host_commit(ctx, L.D, (long long)h.n_done)) != ORQA_OK) return st;
+    ctx->zz_pending = false;
     ctx->clean_delta = delta;
     ctx->stats.last_layer_in = n_in;
     ctx->stats.last_layer_peak = (long long)h.peak;
@@ -1087,6 +1140,7 @@ orqa_status set_from(orqa_ctx* ctx, int64_t n, const uint64_t* x, const uint64_t
     orqa_status st = ORQA_DISPATCH(ctx, merge_input, ctx, s, n, dst, 0.0, &m);  // waits for the stream
     if (st != ORQA_OK) return st;
     if ((st = host_commit(ctx, dst, m)) != ORQA_OK) return st;
+    ctx->zz_pending = false;  // it belonged to the replaced operator
     ctx->clean_delta = 0.0;
     ctx->stats = orqa_stats_t{};
     ctx->err.clear();
@@ -1325,7 +1379,10 @@ orqa_status apply_layer_impl(orqa_ctx* ctx, const orqa_gate* gates, int32_t n_ga
     }
     if (theta && kind != ORQA_RX)
         return fail(ctx, ORQA_EINVAL, "apply_layer_batch: per-problem angles are for ORQA_RX layers only");
-    orqa_status st;
+    orqa_status st = ORQA_OK;
+    if (ctx->relative)
+        st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
     if (ctx->relative)
         st = ORQA_DISPATCH(ctx, apply_layer_relative, ctx, gates, n_gates, delta);
     else if (kind == ORQA_RZZ)
@@ -1368,7 +1425,9 @@ orqa_status orqa_apply_pauli_rotation(orqa_ctx* ctx, const uint64_t* xj, const u
         }
     }
     if (!any) return fail(ctx, ORQA_EINVAL, "apply_pauli_rotation: J is the identity");
-    orqa_status st = ORQA_DISPATCH(ctx, apply_pauli_impl, ctx, xj, zj, theta, delta);
+    orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
+    st = ORQA_DISPATCH(ctx, apply_pauli_impl, ctx, xj, zj, theta, delta);
     if (st != ORQA_OK) return st;
     ctx->stats.n_strings = ctx->n;
     if (n_live_out) *n_live_out = ctx->n;
@@ -1379,10 +1438,12 @@ orqa_status orqa_apply_pauli_rotation(orqa_ctx* ctx, const uint64_t* xj, const u
 orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out) {
     if (!ctx) return ORQA_EINVAL;
     if (!(delta >= 0.0) || std::isinf(delta)) return fail(ctx, ORQA_EINVAL, "merge_truncate: bad delta");
+    orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
     const int dst = (ctx->cur + 1) % 3;
     long long m = 0;
     const double dabs = ctx->relative ? 0.0 : delta;
-    orqa_status st = ORQA_DISPATCH(ctx, merge_state, ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m);
+    st = ORQA_DISPATCH(ctx, merge_state, ctx, ctx->buf[ctx->cur], ctx->n, dst, dabs, &m);
     if (st != ORQA_OK) return st;
     if ((st = host_commit(ctx, dst, m)) != ORQA_OK) return st;
     if (ctx->relative) {
@@ -1402,11 +1463,15 @@ orqa_status orqa_merge_truncate(orqa_ctx* ctx, double delta, int64_t* n_live_out
 orqa_status orqa_expect(orqa_ctx* ctx, double* out) {
     if (!ctx || !out) return ORQA_EINVAL;
     if (ctx->P > 1) return fail(ctx, ORQA_ESTATE, "expect: batched context (use orqa_expect_batch)");
+    const orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
     return ORQA_DISPATCH(ctx, expect_impl, ctx, out);
 }
 
 orqa_status orqa_expect_batch(orqa_ctx* ctx, double* out) {
     if (!ctx || !out) return ORQA_EINVAL;
+    const orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
     return ORQA_DISPATCH(ctx, expect_impl, ctx, out);
 }
 
@@ -1414,6 +1479,8 @@ orqa_status orqa_histogram(orqa_ctx* ctx, int32_t n_bins, double log10_lo, int64
     if (!ctx || !counts) return ORQA_EINVAL;
     if (n_bins < 1 || n_bins > 256 || !(log10_lo < 0.0) || !std::isfinite(log10_lo) || log10_lo < -300.0)
         return fail(ctx, ORQA_EINVAL, "histogram: need 1 <= n_bins <= 256 and -300 <= log10_lo < 0");
+    const orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
     return ORQA_DISPATCH(ctx, histogram_impl, ctx, n_bins, log10_lo, counts, max_abs_out);
 }
 
@@ -1438,6 +1505,8 @@ orqa_status orqa_export_batch(orqa_ctx* ctx, int64_t cap, uint64_t* x, uint64_t*
     *n_out = ctx->n;
     if (ctx->n > cap) return fail(ctx, ORQA_ECAPACITY, "export: operator larger than cap");
     if (ctx->n > 0 && (!x || !z || !c)) return fail(ctx, ORQA_EINVAL, "export: null array");
+    const orqa_status zst = settle_zz(ctx);
+    if (zst != ORQA_OK) return zst;
     int sb = ctx->cur;
     const orqa_status sst = ORQA_DISPATCH(ctx, sorted_buffer, ctx, &sb);
     if (sst != ORQA_OK) return sst;
@@ -1519,6 +1588,13 @@ orqa_status orqa_debug_set(orqa_ctx* ctx, int32_t knob, int64_t value) {
         if (value != 0 && (value < base || value > 63))
             return fail(ctx, ORQA_EINVAL, "debug_set: bucket shift must be 0 or in [default, 63]");
         ctx->fshift = value ? (int)value : base;
+        return ORQA_OK;
+    }
+    case ORQA_DEBUG_NO_ZZ_FUSION: {
+        if (value != 0 && value != 1) return fail(ctx, ORQA_EINVAL, "debug_set: no-fusion is 0 or 1");
+        const orqa_status st = settle_zz(ctx);
+        if (st != ORQA_OK) return st;
+        ctx->zz_fuse = value == 0;
         return ORQA_OK;
     }
     default:
@@ -1628,8 +1704,9 @@ orqa_status prepare_program(orqa_ctx* ctx, const orqa_layer_desc* d, int nl, int
 
 uint64_t program_key(const orqa_ctx* ctx, const orqa_layer_desc* d, int nl, int repeat, double delta) {
     uint64_t h = 0xcbf29ce484222325ull;
-    const int head[12] = {ctx->W, ctx->P, ctx->fp32 ? 1 : 0, ctx->cur, repeat, ctx->range_target, ctx->sub_max,
-                          ctx->n_fine, ctx->grid_per_sm, ctx->fshift, ctx->pass_limit, ctx->track_norm ? 1 : 0};
+    const int head[13] = {ctx->W, ctx->P, ctx->fp32 ? 1 : 0, ctx->cur, repeat, ctx->range_target, ctx->sub_max,
+                          ctx->n_fine, ctx->grid_per_sm, ctx->fshift, ctx->pass_limit, ctx->track_norm ? 1 : 0,
+                          ctx->zz_fuse ? 1 : 0};
     h = fnv(h, head, sizeof head);
     h = fnv(h, &delta, sizeof delta);
     for (int l = 0; l < nl; ++l) {
@@ -1639,6 +1716,14 @@ uint64_t program_key(const orqa_ctx* ctx, const orqa_layer_desc* d, int nl, int 
         if (d[l].theta) h = fnv(h, d[l].theta, sizeof(double) * (size_t)d[l].n_gates * (size_t)ctx->P);
     }
     return h;
+}
+
+// Whether the ZZ layer li of repetition r is held back for the entry split
+// of the X layer that follows it at once (no expectation between them).
+bool program_holds_zz(const orqa_ctx* ctx, const std::vector<ProgLayer>& pl, size_t li, int r, int repeat) {
+    const ProgLayer& L = pl[li];
+    const ProgLayer* nx = li + 1 < pl.size() ? &pl[li + 1] : (r + 1 < repeat ? &pl[0] : nullptr);
+    return L.kind == ORQA_RZZ && ctx->zz_fuse && !L.expect_after && L.zz.size() == 1 && nx && nx->kind == ORQA_RX;
 }
 
 #define CAPTURE_TRY(expr)                                                           \
@@ -1661,22 +1746,32 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
     const int g_stream = ctx->sm_count * ctx->grid_per_sm;
     const int g_local = ctx->sm_count * LB_CTAS_PER_SM;
     cudaGraph_t graph = nullptr;
+    const ZZGroups* held = nullptr;  // a ZZ layer left to the next entry split
     ctx->profile = false;
     ctx->stream = cs;
     CAPTURE_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < repeat; ++r) {
-        for (const ProgLayer& L : pl) {
+        for (size_t li = 0; li < pl.size(); ++li) {
+            const ProgLayer& L = pl[li];
             if (L.kind == ORQA_RZZ) {
-                for (const ZZGroups& gz : L.zz)
-                    k_rzz_layer<W, T><<<g_stream, 256, 0, cs>>>(ctx->buf[cur], ctx->cap, ctx->ctr, gz);
+                if (program_holds_zz(ctx, pl, li, r, repeat))
+                    held = &L.zz[0];
+                else
+                    for (const ZZGroups& gz : L.zz)
+                        k_rzz_layer<W, T><<<g_stream, 256, 0, cs>>>(ctx->buf[cur], ctx->cap, ctx->ctr, gz);
                 k_layer_end_zz<<<1, 32, 0, cs>>>(ctx->ctr, L.ng, ctx->prog_stats);
                 CAPTURE_TRY(cudaGetLastError());
             } else {
                 const RxLists X = rx_lists(ctx, cur);
                 k_layer_begin<<<1, 128, 0, cs>>>(ctx->ctr, ctx->pop_delta);
                 CAPTURE_TRY(cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 2, cs));
-                k_rx_split<W, T><<<g_stream, 256, 0, cs>>>(X.src, X.done, X.act, ctx->cap, L.rx, ctx->ctr,
-                                                           ctx->fcount, ctx->fshift);
+                if (held)
+                    k_rx_split<W, T, true><<<g_stream, 256, 0, cs>>>(X.src, X.done, X.act, ctx->cap, L.rx, ctx->ctr,
+                                                                     ctx->fcount, ctx->fshift, *held);
+                else
+                    k_rx_split<W, T, false><<<g_stream, 256, 0, cs>>>(X.src, X.done, X.act, ctx->cap, L.rx,
+                                                                      ctx->ctr, ctx->fcount, ctx->fshift, kNoZZ);
+                held = nullptr;
                 CAPTURE_TRY(cudaGetLastError());
                 cudaStreamCaptureStatus cst;
                 cudaGraph_t g = nullptr;
@@ -1750,6 +1845,7 @@ orqa_status run_program_impl(orqa_ctx* ctx, const orqa_layer_desc* d, int nl, in
     if (st != ORQA_OK) return st;
     if (n_expect > 0 && (!out || n_out < n_expect))
         return fail(ctx, ORQA_EINVAL, "run_program: expect_out too short");
+    if ((st = settle_zz(ctx)) != ORQA_OK) return st;
     // A first ZZ layer meets strings below delta only if the operator was
     // never truncated at delta; dropping them before the layer is the same
     // as after it (a ZZ layer maps strings one to one with |c| unchanged).
@@ -1826,6 +1922,14 @@ orqa_status run_program_impl(orqa_ctx* ctx, const orqa_layer_desc* d, int nl, in
     ctx->stats.dropped_sum_sq = ctx->track_norm ? ps.dropped_sq : std::nan("");
     ctx->stats.n_strings = ctx->n;
     if (h.err) {
+        // an X layer that stopped after a ZZ layer held back for it: that
+        // layer is complete but not yet applied to the committed buffer
+        const long long k = (long long)h.n_layers, nlay = (long long)pl.size();
+        if (k >= 1 && k < nlay * repeat && program_holds_zz(ctx, pl, (size_t)((k - 1) % nlay), (int)((k - 1) / nlay),
+                                                           repeat)) {
+            ctx->zz_pend = pl[(size_t)((k - 1) % nlay)].zz[0];
+            ctx->zz_pending = true;
+        }
         char where[96];
         snprintf(where, sizeof where, "program (stopped after %u of %lld layers)", h.n_layers,
                  (long long)nl * repeat);
@@ -2043,7 +2147,9 @@ orqa_status orqa_shard_split(orqa_ctx* ctx, int32_t n_ranks, int32_t rank, int64
     if (n_ranks < 1 || n_ranks > SHARD_MAX_RANKS || rank < 0 || rank >= n_ranks || send_cap < 0 || !send_counts)
         return fail(ctx, ORQA_EINVAL, "shard_split: bad arguments");
     if (ctx->P > 1) return fail(ctx, ORQA_ESTATE, "shard_split: not for batched contexts");
-    const orqa_status st = ORQA_DISPATCH(ctx, shard_split_impl, ctx, n_ranks, rank, send_cap, send, send_counts);
+    orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
+    st = ORQA_DISPATCH(ctx, shard_split_impl, ctx, n_ranks, rank, send_cap, send, send_counts);
     if (st == ORQA_OK) ctx->err.clear();
     return st;
 }
@@ -2053,7 +2159,9 @@ orqa_status orqa_shard_append(orqa_ctx* ctx, int64_t n, const uint64_t* recv) {
     if (n < 0 || (n > 0 && !recv)) return fail(ctx, ORQA_EINVAL, "shard_append: bad arguments");
     if (ctx->P > 1) return fail(ctx, ORQA_ESTATE, "shard_append: not for batched contexts");
     if (ctx->n + n > ctx->cap) return fail(ctx, ORQA_ECAPACITY, "shard_append: result exceeds capacity");
-    const orqa_status st = ORQA_DISPATCH(ctx, shard_append_impl, ctx, n, recv);
+    orqa_status st = settle_zz(ctx);
+    if (st != ORQA_OK) return st;
+    st = ORQA_DISPATCH(ctx, shard_append_impl, ctx, n, recv);
     if (st == ORQA_OK) ctx->err.clear();
     return st;
 }

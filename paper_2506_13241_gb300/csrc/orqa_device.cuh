@@ -213,6 +213,56 @@ __device__ __forceinline__ void shl_planes(const uint64_t (&v)[W], int d, uint64
     }
 }
 
+// One ZZ layer of Clifford angles on one string, in closed form (the rule
+// is derived above k_rzz_layer): z becomes z xor C0 per set, and the return
+// value is 1 iff the coefficient changes sign.
+template <int W>
+__device__ __forceinline__ unsigned zz_conjugate(const ZZGroups& G, const uint64_t (&x)[W], uint64_t (&z)[W]) {
+    unsigned neg = 0;
+    int g = 0;
+    for (int k = 0; k < G.n_sets; ++k) {
+        uint64_t c0[W], c1[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) c0[w] = c1[w] = 0;
+        for (; g < G.set_end[k]; ++g) {
+            const int d = G.d[g];
+            uint64_t sh[W], a[W], b[W];
+            shr_planes<W>(x, d, sh);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                a[w] = (x[w] ^ sh[w]) & G.mask[g][w];
+                c1[w] ^= c0[w] & a[w];
+                c0[w] ^= a[w];
+            }
+            shl_planes<W>(a, d, b);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                c1[w] ^= c0[w] & b[w];
+                c0[w] ^= b[w];
+            }
+        }
+        const int mode = G.set_mode[k];
+        unsigned par = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t t;
+            if (mode == 1)
+                t = x[w] & c0[w];
+            else if (mode == 2)
+                t = x[w] & ((z[w] & c0[w]) ^ c1[w]);
+            else
+                t = x[w] & ((z[w] & c0[w]) ^ c1[w] ^ c0[w]);
+            par ^= (unsigned)__popcll(t);
+        }
+        neg ^= par & 1u;
+        if (mode != 1) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) z[w] ^= c0[w];
+        }
+    }
+    return neg;
+}
+
 template <int W>
 __device__ __forceinline__ int bit_of(const uint64_t (&v)[W], int q) {
     if constexpr (W == 1) {

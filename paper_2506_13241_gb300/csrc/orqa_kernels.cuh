@@ -43,48 +43,7 @@ __global__ void __launch_bounds__(256) k_rzz_layer(StrList s, long long cap, Cou
         uint64_t x[W], z[W];
         load_plane<W>(s.x, i, x);
         load_plane<W>(s.z, i, z);
-        unsigned neg = 0;
-        int g = 0;
-        for (int k = 0; k < G.n_sets; ++k) {
-            uint64_t c0[W], c1[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) c0[w] = c1[w] = 0;
-            for (; g < G.set_end[k]; ++g) {
-                const int d = G.d[g];
-                uint64_t sh[W], a[W], b[W];
-                shr_planes<W>(x, d, sh);
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    a[w] = (x[w] ^ sh[w]) & G.mask[g][w];
-                    c1[w] ^= c0[w] & a[w];
-                    c0[w] ^= a[w];
-                }
-                shl_planes<W>(a, d, b);
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    c1[w] ^= c0[w] & b[w];
-                    c0[w] ^= b[w];
-                }
-            }
-            const int mode = G.set_mode[k];
-            unsigned par = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                uint64_t t;
-                if (mode == 1)
-                    t = x[w] & c0[w];
-                else if (mode == 2)
-                    t = x[w] & ((z[w] & c0[w]) ^ c1[w]);
-                else
-                    t = x[w] & ((z[w] & c0[w]) ^ c1[w] ^ c0[w]);
-                par ^= (unsigned)__popcll(t);
-            }
-            neg ^= par & 1u;
-            if (mode != 1) {
-#pragma unroll
-                for (int w = 0; w < W; ++w) z[w] ^= c0[w];
-            }
-        }
+        const unsigned neg = zz_conjugate<W>(G, x, z);
         store_plane<W>(s.z, i, z);
         if (neg) {
             T* c = reinterpret_cast<T*>(s.c) + i;
@@ -665,8 +624,9 @@ __global__ void k_layer_end_x(Counters* ctr, int cur, uint64_t mask0, uint64_t m
     ps->x_layers += 1;
 }
 
-// End of a ZZ layer inside a captured program (applied in place: |O| and
-// the buffer are unchanged).
+// End of a ZZ layer inside a captured program (applied in place, or held
+// back for the next X layer's entry split: |O| and the buffer are
+// unchanged).
 __global__ void k_layer_end_zz(Counters* ctr, int n_gates, ProgramStats* ps) {
     if (threadIdx.x != 0 || blockIdx.x != 0 || ctr->err) return;
     ctr->n_layers += 1;

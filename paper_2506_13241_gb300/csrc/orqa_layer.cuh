@@ -107,12 +107,17 @@ __device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& t
 // Each block takes tiles of SPLIT_ITEMS strings per thread: all loads of a
 // tile are issued before any decision, and the tile's outputs are reserved
 // with one atomic per list (a block scan gives every string its slot).
+// ZZ: a ZZ layer of Clifford angles (G) that precedes the X layer is applied
+// here first, string by string (zz_conjugate), instead of by a pass of its
+// own over the operator: it maps each string to one string with |c|
+// unchanged, so the routing below sees exactly the strings that the layer
+// on its own would have left.
 constexpr int SPLIT_ITEMS = 4;
 
-template <int W, typename T>
+template <int W, typename T, bool ZZ>
 __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, StrList active, long long cap,
                                                   const __grid_constant__ RxRun run, Counters* ctr,
-                                                  uint32_t* fcount, int fshift) {
+                                                  uint32_t* fcount, int fshift, const __grid_constant__ ZZGroups G) {
     __shared__ int warp_tot[33];
     __shared__ unsigned long long s_base[2];
     if (block_aborted(ctr)) return;
@@ -124,6 +129,7 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
     double my_drop_sq = 0.0;
     for (long long t0 = (long long)blockIdx.x * tile; t0 < n; t0 += (long long)gridDim.x * tile) {  // block-uniform
         uint64_t z[SPLIT_ITEMS][W];
+        uint64_t xz[ZZ ? SPLIT_ITEMS : 1][W];  // x, loaded up front only for the ZZ stage
         T c[SPLIT_ITEMS];
         int kind[SPLIT_ITEMS];  // 0: not live or dropped, 1: output list, 2: active list
 #pragma unroll
@@ -136,6 +142,7 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
             if (i < n) {
                 load_plane<W>(src.z, i, z[k]);
                 c[k] = sc[i];
+                if constexpr (ZZ) load_plane<W>(src.x, i, xz[k]);
             }
         }
         int nd = 0, na = 0;
@@ -143,6 +150,9 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
         for (int k = 0; k < SPLIT_ITEMS; ++k) {
             const long long i = t0 + (long long)k * blockDim.x + threadIdx.x;
             if (i >= n) continue;
+            if constexpr (ZZ) {
+                if (zz_conjugate<W>(G, xz[k], z[k])) c[k] = Coef<T>::negate(c[k]);
+            }
             uint64_t f[W], acc = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -180,7 +190,12 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
             StrList dst = act ? active : done;
             const unsigned pid = src.pid ? src.pid[i] : 0u;
             uint64_t x[W];
-            load_plane<W>(src.x, i, x);
+            if constexpr (ZZ) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) x[w] = xz[k][w];
+            } else {
+                load_plane<W>(src.x, i, x);
+            }
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, z[k]);

@@ -34,7 +34,7 @@ EXPORTED = ["orqa_workspace_bytes", "orqa_create", "orqa_set_operator", "orqa_se
             "orqa_shard_owner", "orqa_shard_split", "orqa_shard_append", "orqa_counters"]
 ORQA_SHARD_MAX_RANKS = 512
 ORQA_DEBUG_SPIN_LIMIT, ORQA_DEBUG_POISON_MERGE_TABLE, ORQA_DEBUG_MERGE_TABLE_SLOTS = 1, 2, 3
-ORQA_DEBUG_PASS_LIMIT, ORQA_DEBUG_BUCKET_SHIFT = 4, 5
+ORQA_DEBUG_PASS_LIMIT, ORQA_DEBUG_BUCKET_SHIFT, ORQA_DEBUG_NO_ZZ_FUSION = 4, 5, 6
 ORQA_NOALLOC_MAX_STRINGS = 1 << 27
 ORQA_MAX_PROBLEMS = 4096
 
