@@ -92,7 +92,6 @@ struct orqa_ctx {
     size_t shared_bytes = 0;           // size of the layer / merge scratch region
     size_t local_smem = 0;
     Counters* ctr = nullptr;
-    unsigned long long* pop_delta = nullptr;
     double* partials = nullptr;
     double* scalar = nullptr;
     // batched contexts: per-problem rotation tables, expectation partials,
@@ -234,7 +233,6 @@ Layout layout(int n_qubits, long long cap, int P) {
     t += align_up(((size_t)SCAN_TILE + 1) * 8);  // scan tile sums
     t += align_up(((size_t)(cap / MIN_RANGE_TARGET) + 2) * 4);  // unit-kernel range starts
     t += align_up(sizeof(Counters));
-    t += align_up(MAX_QUBITS * 8);
     t += align_up(EXPECT_BLOCKS * 8);
     t += align_up(64);
     t += align_up(PROGRAM_RESULTS * 8) + align_up(sizeof(ProgramStats));
@@ -764,11 +762,11 @@ orqa_status enqueue_pass(orqa_ctx* ctx, const RxLists& L, const RxRun& run, int 
     if (run.track_norm)
         k_bucket_local<W, T, true><<<local_grid_n, LB_THREADS, ctx->local_smem, ctx->stream>>>(
             ctx->records, ctx->foffsets, ctx->range_start, ctx->n_fine, ctx->range_target, ctx->sub_max, run, L.done,
-            L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
+            L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift);
     else
         k_bucket_local<W, T, false><<<local_grid_n, LB_THREADS, ctx->local_smem, ctx->stream>>>(
             ctx->records, ctx->foffsets, ctx->range_start, ctx->n_fine, ctx->range_target, ctx->sub_max, run, L.done,
-            L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift, ctx->pop_delta);
+            L.act, ctx->cap, ctx->ctr, ctx->fcount, ctx->fshift);
     prof_end(ctx, *r_lo);
     LAUNCH_CHECK(ctx);
     k_pass_advance<<<1, 32, 0, ctx->stream>>>(ctx->ctr, 0, cond, use_cond, ctx->pass_limit);
@@ -785,7 +783,6 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
     const RxLists L = rx_lists(ctx, ctx->cur);
     const long long n_in = ctx->n;
     if (reset_counters(ctx) != ORQA_OK) return ORQA_ECUDA;
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->pop_delta, 0, MAX_QUBITS * 8, ctx->stream));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 2, ctx->stream));
     int r_split = -1;
     const bool fused = ctx->zz_pending;  // a held-back ZZ layer is applied by the split
@@ -839,19 +836,8 @@ orqa_status apply_rx(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta, co
         if ((st = check_flags(ctx, h, "rotation layer")) != ORQA_OK) return st;
         ++pass;
     }
-    // Sum over the gates of |O| before each gate: |O| changes at gate q by
-    // the population delta recorded there (and by the strings the entry
-    // split dropped at the first gate).
-    std::vector<unsigned long long> pd(MAX_QUBITS);
-    CUDA_TRY(ctx, cudaMemcpyAsync(pd.data(), ctx->pop_delta, MAX_QUBITS * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    long long pop = n_in, updates = 0;
-    for (int k = 0; k < ng; ++k) {
-        updates += pop;
-        const int q = g[k].q0;
-        pop += (long long)pd[q];
-        if (k == 0) pop -= (long long)h.split_dropped;
-    }
+    // Sum over the gates of |O| before each gate (Counters::upd_w)
+    const long long updates = (long long)ng * n_in - (long long)h.split_dropped * (ng - 1) + (long long)h.upd_w;
     if ((st = host_commit(ctx, L.D, (long long)h.n_done)) != ORQA_OK) return st;
     ctx->zz_pending = false;
     ctx->clean_delta = delta;
@@ -1205,11 +1191,15 @@ namespace {
 template <int W, typename T>
 cudaError_t set_local_smem(orqa_ctx* ctx) {
     ctx->local_smem = sizeof(LocalSmem<W, T>);
-    cudaError_t e = cudaFuncSetAttribute(k_bucket_local<W, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ctx->local_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_bucket_local<W, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ctx->local_smem);
+    // all of the SM's unified memory that can be shared memory: the unit
+    // kernel's occupancy is bound by it
+    for (const void* f : {(const void*)k_bucket_local<W, T, false>, (const void*)k_bucket_local<W, T, true>}) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->local_smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -1301,7 +1291,6 @@ orqa_status orqa_create(const orqa_config* cfg, orqa_ctx** out) {
     ctx->tile_sums = (long long*)p; p += align_up(((size_t)SCAN_TILE + 1) * 8);
     ctx->range_start = (int32_t*)p; p += align_up(((size_t)(cfg->capacity / MIN_RANGE_TARGET) + 2) * 4);
     ctx->ctr = (Counters*)p; p += align_up(sizeof(Counters));
-    ctx->pop_delta = (unsigned long long*)p; p += align_up(MAX_QUBITS * 8);
     ctx->partials = (double*)p; p += align_up(EXPECT_BLOCKS * 8);
     ctx->scalar = (double*)p; p += align_up(64);
     ctx->prog_results = (double*)p; p += align_up(PROGRAM_RESULTS * 8);
@@ -1763,7 +1752,7 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
                 CAPTURE_TRY(cudaGetLastError());
             } else {
                 const RxLists X = rx_lists(ctx, cur);
-                k_layer_begin<<<1, 128, 0, cs>>>(ctx->ctr, ctx->pop_delta);
+                k_layer_begin<<<1, 32, 0, cs>>>(ctx->ctr);
                 CAPTURE_TRY(cudaMemsetAsync(ctx->fcount, 0, (size_t)ctx->n_fine * 2, cs));
                 if (held)
                     k_rx_split<W, T, true><<<g_stream, 256, 0, cs>>>(X.src, X.done, X.act, ctx->cap, L.rx, ctx->ctr,
@@ -1804,8 +1793,7 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
                 }
                 CAPTURE_TRY(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
                                                                 cudaStreamSetCaptureDependencies));
-                k_layer_end_x<<<1, 32, 0, cs>>>(ctx->ctr, X.D, L.rx.mask[0], L.rx.mask[1], ctx->pop_delta,
-                                                ctx->prog_stats);
+                k_layer_end_x<<<1, 32, 0, cs>>>(ctx->ctr, X.D, L.ng, ctx->prog_stats);
                 CAPTURE_TRY(cudaGetLastError());
                 cur = X.D;
             }

@@ -56,6 +56,12 @@ struct Counters {
     unsigned long long peak;         // largest output + active count seen in the layer
     unsigned long long n_in;         // |O| entering the layer (captured programs)
     double dropped_sq;               // sum of c^2 over the strings truncation removed
+    // The layer's string-gate updates are the sum over its gates (ascending
+    // qubits) of |O| before the gate: ng n_in - split_dropped (ng - 1) +
+    // upd_w, where upd_w sums, over every unit and gate, the unit's
+    // population change at that gate times the number of the layer's gates
+    // above it (two's complement: the sum may be negative).
+    unsigned long long upd_w;
     unsigned int range_cursor;       // next CTA range of the unit kernel
     int pass;                        // chunk pass in progress
     unsigned int err;                // ERR_* bits
@@ -211,6 +217,13 @@ __device__ __forceinline__ void shl_planes(const uint64_t (&v)[W], int d, uint64
             r[0] = v[0] << d;
         }
     }
+}
+
+// Number of the run's gates (set bits of its 128-bit qubit mask) above q.
+__device__ __forceinline__ int gates_above(const uint64_t (&m)[2], int q) {
+    const uint64_t lo = q >= 64 ? 0ull : (q == 63 ? 0ull : m[0] >> (q + 1));
+    const uint64_t hi = q >= 64 ? (q == 127 ? 0ull : m[1] >> (q - 63)) : m[1];
+    return __popcll(lo) + __popcll(hi);
 }
 
 // One ZZ layer of Clifford angles on one string, in closed form (the rule

@@ -578,38 +578,24 @@ __global__ void __launch_bounds__(256) k_histogram(const T* c, long long cap, co
 // Start of an X layer inside a captured program: clears the layer counters
 // (not the error bits or the committed operator) and the per-qubit
 // population deltas, and records |O| entering the layer.
-__global__ void k_layer_begin(Counters* ctr, unsigned long long* pop_delta) {
-    const int t = threadIdx.x;
-    if (blockIdx.x != 0) return;
-    for (int q = t; q < MAX_QUBITS; q += blockDim.x) pop_delta[q] = 0ull;
-    if (t != 0) return;
+__global__ void k_layer_begin(Counters* ctr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     ctr->n_done = ctr->n_next = ctr->n_units = ctr->unit_cursor = 0;
     ctr->branch_events = ctr->dropped = ctr->pairs_one = ctr->pairs_two = 0;
-    ctr->n_active = ctr->split_dropped = ctr->peak = 0;
+    ctr->n_active = ctr->split_dropped = ctr->peak = ctr->upd_w = 0;
+    ctr->dropped_sq = 0.0;
     ctr->n_in = ctr->n_live;
     ctr->range_cursor = 0;
     ctr->pass = 0;
 }
 
-// End of an X layer inside a captured program: commits its output list
-// (buffer `cur`) and adds the layer to the program totals.  The updates are
-// the sum over the run's gates (ascending qubits of mask) of |O| before the
-// gate: |O| changes at gate q by the population delta recorded there, and
-// by the strings the entry split dropped at the first gate.
-__global__ void k_layer_end_x(Counters* ctr, int cur, uint64_t mask0, uint64_t mask1,
-                              const unsigned long long* pop_delta, ProgramStats* ps) {
+// End of an X layer of ng gates inside a captured program: commits its
+// output list (buffer `cur`) and adds the layer to the program totals (the
+// updates as Counters::upd_w states).
+__global__ void k_layer_end_x(Counters* ctr, int cur, int ng, ProgramStats* ps) {
     if (threadIdx.x != 0 || blockIdx.x != 0 || ctr->err) return;
-    unsigned long long pop = ctr->n_in, upd = 0;
-    bool first = true;
-    for (int w = 0; w < 2; ++w) {
-        for (uint64_t m = w ? mask1 : mask0; m; m &= m - 1) {
-            const int q = 64 * w + __ffsll((long long)m) - 1;
-            upd += pop;
-            pop += pop_delta[q];
-            if (first) pop -= ctr->split_dropped;
-            first = false;
-        }
-    }
+    const unsigned long long upd = (unsigned long long)ng * ctr->n_in -
+                                   ctr->split_dropped * (unsigned long long)(ng - 1) + ctr->upd_w;
     ctr->n_live = ctr->n_done;
     ctr->cur = cur;
     ctr->n_layers += 1;

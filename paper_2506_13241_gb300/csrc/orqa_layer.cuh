@@ -43,7 +43,6 @@ constexpr int LB_TABLE = 512;       // shared-memory hash slots (load <= 1/2)
 constexpr int LB_UPW = 16;          // units a warp owns per round (lanes 0..15)
 constexpr int LB_UPW_LOG = 4;
 constexpr int LB_RU = LB_WARPS * LB_UPW;  // dense unit rows (LB_UPW per warp)
-constexpr int LB_LIST = LB_UPW * 16;      // most pairs of one level in a warp
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -339,7 +338,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(uint32_t* offsets, co
 // W = 2, exactly 32 bytes for W = 1 -- so the scattered writes never leave a
 // partly written sector.
 // ---------------------------------------------------------------------------
-constexpr int SCATTER_ILP = 8;
+constexpr int SCATTER_ILP = 4;
 
 template <int W, typename T>
 __device__ __forceinline__ void store_record(void* base, long long i, const uint64_t (&x)[W],
@@ -506,11 +505,9 @@ struct LocalSmem {
     int16_t ustart[LB_MAX + 1]; // first position of each unit in that order
     int32_t rep_cnt[LB_MAX / 2]; // strings per representative, two 16-bit counts per word
     uint16_t spid[LB_MAX];      // problem index of each string
-    uint16_t list[LB_WARPS][LB_LIST];  // pairs of the current level, per warp
     Rot<T> hrot[LB_RU];         // cos and sin of the current level's gate, per unit
     Rot<T> srot[MAX_QUBITS];    // cos and sin per qubit (contexts with one problem)
     uint8_t s_idx[LB_MAX];
-    int blk_delta[MAX_QUBITS];
     int warp_tot[33];
     double drop_sq[LB_WARPS];   // per warp: sum of c^2 dropped (norm tracking only)
     int group_cursor;           // next unit group a warp claims
@@ -635,7 +632,7 @@ template <int W, typename T, bool TRACK>
 __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const void* bk, const uint32_t* __restrict__ offsets, const int32_t* __restrict__ range_start,
     long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
-    StrList next, long long cap, Counters* ctr, uint32_t* fcount_next, int fshift, unsigned long long* pop_delta) {
+    StrList next, long long cap, Counters* ctr, uint32_t* fcount_next, int fshift) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LocalSmem<W, T>& S = *reinterpret_cast<LocalSmem<W, T>*>(smem_raw);
     if (block_aborted(ctr)) return;
@@ -645,15 +642,13 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const long long J = ((long long)offsets[n_fine] + range_target - 1) / range_target;
 
     const bool batched = run.tab.f64 != nullptr;
-    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS) {
-        S.blk_delta[t] = 0;
+    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)
         S.srot[t] = Coef<T>::rot(run, 0u, t);  // one read of the parameter table per qubit
-    }
     // per-lane event counts stay far below 2^32 (a launch handles at most
     // 5 entries per string of the capacity, < 2^31, spread over every lane of
     // the grid); the warp totals are summed in 64 bits
     unsigned my_branch = 0, my_drop = 0;
-    unsigned long long my_one = 0, my_two = 0;
+    unsigned long long my_one = 0, my_two = 0, my_upd = 0;  // my_upd: see Counters::upd_w
     if (TRACK && tid < LB_WARPS) S.drop_sq[tid] = 0.0;
     // The work items are sub-ranges; the next one (claiming a new range when
     // the current range is done) is prepared by warp LB_WARPS - 1 while the
@@ -830,7 +825,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             const unsigned mj = level_mask(j);
             const bool act = own && np > j;
             unsigned sgl = 0, dbl = 0, hi = 0;
-            int pop_before = 0;
+            int pop_before = 0, qj = 0;
             if (act) {
                 const unsigned o = S.occ[ub + lane];
                 const unsigned lo = o & mj;
@@ -838,33 +833,44 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 sgl = lo ^ hi;
                 dbl = lo & hi;
                 pop_before = __popc(o);
-                const int qj = packed_pos(ppos, j);
+                qj = packed_pos(ppos, j);
                 S.hrot[ub + lane] = batched ? Coef<T>::rot(run, upid, qj) : S.srot[qj];
             }
             unsigned tot;
-            unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
+            const unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
             const unsigned n1 = tot & 0xffffu, n2 = tot >> 16;
-            // one list per warp: the one-member pairs at [0, n1), the
-            // two-member pairs at [n1, n1 + n2); an entry is
-            // (lane << 6) | (sigma_y side of a lone member << 5) | slot
-            unsigned o1 = o12 & 0xffffu, o2 = n1 + (o12 >> 16);
             my_one += n1;
             my_two += n2;
-            for (unsigned b = sgl | dbl; b; b &= b - 1) {
-                const int l = __ffs(b) - 1;
-                const bool d = (dbl >> l) & 1u;
-                S.list[wp][d ? o2 : o1] = (uint16_t)((lane << 6) | (d ? 0u : ((hi >> l) & 1u) << 5) | l);
-                o1 += d ? 0u : 1u;
-                o2 += d ? 1u : 0u;
-            }
-            __syncwarp();
+            __syncwarp();  // the owners' hrot entries are visible
+            // entry t of the level: the one-member pairs at [0, n1), the
+            // two-member pairs at [n1, n1 + n2), each kind in owner-lane
+            // order; a lane finds its entry's owner by a binary search of
+            // the owners' exclusive counts and its slot as the r-th set bit
             for (unsigned t0 = 0; t0 < n1 + n2; t0 += 32) {  // warp-uniform
                 const unsigned t = t0 + lane;
-                if (t >= n1 + n2) continue;
                 const bool two = t >= n1;
-                const int e = S.list[wp][t];
-                const int ur = ub + (e >> 6), la = e & 31;
-                const bool y_side = (e & 32) != 0;
+                const unsigned rk = two ? t - n1 : t;
+                const int sh = two ? 16 : 0;
+                int lo = 0, hi2 = LB_UPW - 1;
+                unsigned base = 0;  // exclusive count of owner lo (lane 0: 0)
+#pragma unroll
+                for (int step = 0; step < LB_UPW_LOG; ++step) {
+                    const int mid = (lo + hi2 + 1) >> 1;
+                    const unsigned fm = (__shfl_sync(FULL_MASK, o12, mid) >> sh) & 0xffffu;
+                    if (fm <= rk) {
+                        lo = mid;
+                        base = fm;
+                    } else {
+                        hi2 = mid - 1;
+                    }
+                }
+                const unsigned ms = __shfl_sync(FULL_MASK, sgl, lo);
+                const unsigned md = __shfl_sync(FULL_MASK, dbl, lo);
+                const unsigned mh = __shfl_sync(FULL_MASK, hi, lo);
+                if (t >= n1 + n2) continue;
+                const int la = nth_set_bit32(two ? md : ms, (int)(rk - base));
+                const int ur = ub + lo;
+                const bool y_side = !two && ((mh >> la) & 1u);
                 const int lb = la | bit;
                 const T u1 = S.dense[ur][dcol(ur, y_side ? lb : la)];
                 T na, nb;
@@ -894,7 +900,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             if (act) {
                 const int d = __popc(S.occ[ub + lane]) - pop_before;
                 my_branch += (unsigned)pop_before;
-                if (d) atomicAdd(&S.blk_delta[packed_pos(ppos, j)], d);
+                my_upd += (unsigned long long)((long long)d * gates_above(run.mask, qj));
             }
         }
         // ---- outputs: flattened over the warp, one reservation per warp and list
@@ -980,9 +986,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         atomicAdd(&ctr->pairs_two, my_two);
         if (TRACK) atomicAdd(&ctr->dropped_sq, S.drop_sq[wp]);
     }
-    __syncthreads();
-    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)
-        if (S.blk_delta[t]) atomicAdd(&pop_delta[t], (unsigned long long)(long long)S.blk_delta[t]);
+    const unsigned long long nu = warp_sum64(my_upd);
+    if (lane == 0 && nu) atomicAdd(&ctr->upd_w, nu);
 }
 
 }  // namespace orqa

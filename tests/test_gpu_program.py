@@ -83,6 +83,36 @@ def test_program_updates_match_layer_calls(orqa):
     assert ctx.stats()["string_gate_updates"] == total
 
 
+def test_update_counts_match_oracle(orqa, oracle_mod):
+    """The string-gate update count of a layer is the sum over its gates of
+    |O| before the gate: taken from the oracle gate by gate (heavy-hex,
+    theta = pi/4, 4 steps, delta = 1e-4, so strings branch, merge and drop
+    inside the layers), it equals the CUDA path's count for every layer
+    applied by a call, and their total equals a captured program's count."""
+    wl = W.workload("heavyhex")
+    n, delta = wl["n"], 1e-4
+    op = oracle_mod.Oracle(n)
+    for lab, c in wl["observable"]:
+        op.add_label(lab, c)
+    ctx = orqa.Context(n, 1 << 20)
+    ctx.set_labels(wl["observable"])
+    total = 0
+    for t in range(4):
+        for layer in wl["layers"]:
+            expected = 0
+            for g in layer:
+                expected += len(op)
+                op.apply(g, delta)
+            ctx.apply_layer(layer, delta)
+            got = ctx.counters()["string_gate_updates"]
+            assert got == expected, (t, layer[0][0], got, expected)
+            total += expected
+    prog_ctx = orqa.Context(n, 1 << 20)
+    prog_ctx.set_labels(wl["observable"])
+    prog_ctx.run_program(kicked_program(orqa, prog_ctx, wl["layers"]), 4, delta)
+    assert prog_ctx.counters()["string_gate_updates"] == total
+
+
 def test_batched_program(orqa, oracle_mod):
     """theta x observable sweep (4 angles x weights 1, 3, 5; 3 steps;
     delta = 1e-4) as one graph: bit-exact per problem against the oracle."""
