@@ -35,7 +35,7 @@ namespace orqa {
 // at the 1e9-string heavy-hex workload than 8 warps x 3 CTAs, and faster
 // than 32 units per warp).
 constexpr int LB_THREADS = 128;
-constexpr int LB_CTAS_PER_SM = 6;  // resident unit-kernel CTAs per SM (launch bound)
+constexpr int LB_CTAS_PER_SM = 7;  // resident unit-kernel CTAs per SM (launch bound)
 constexpr int LB_WARPS = LB_THREADS / 32;
 constexpr int LB_MAX = 256;         // most strings one CTA sub-range may hold
 constexpr int LB_TARGET = 448;      // strings per CTA range, on average (default tuning)
@@ -48,6 +48,21 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ int fine_bucket(uint64_t h, int fshift) { return (int)(h >> fshift); }
+
+// A string that a chunk pass sends on to the next carries its slot in its
+// next unit (the bits of x at the next chunk's positions) in bits 10..14 of
+// its unit-key hash, and its x with those bits cleared (the next unit key's
+// x): the unit kernel knows both once per unit, so the next pass's load
+// needs no chunk search.  (The entry split writes full x; pass 0 searches.)
+// Fine buckets use the top bits of the hash, shared-memory slots the low 9
+// bits and the problem index bits 16..31.
+constexpr int IDX_SHIFT = 10;
+
+__device__ __forceinline__ uint64_t with_idx(uint64_t h, unsigned idx) {
+    return (h & ~(0x1full << IDX_SHIFT)) | ((uint64_t)(idx & 31u) << IDX_SHIFT);
+}
+
+__device__ __forceinline__ int idx_of(uint64_t h) { return (int)(h >> IDX_SHIFT) & 31; }
 
 // Fine-bucket counts are 16-bit, two per 32-bit word (half the footprint of
 // the randomly addressed count array).  A bucket holds at most sub_max <= 512
@@ -499,14 +514,17 @@ struct LocalSmem {
     alignas(4) uint16_t table[LB_TABLE];  // hash table of string indices (0xffff: empty), then unit masks
     unsigned occ[LB_RU];
     int16_t s_unit[LB_MAX];     // home slot, then representative, then unit id
-    int16_t rep_uid[LB_MAX];    // unit id of a representative
     int16_t u_rep[LB_MAX];
     int16_t s_order[LB_MAX];    // the strings in unit order
     int16_t ustart[LB_MAX + 1]; // first position of each unit in that order
-    int32_t rep_cnt[LB_MAX / 2]; // strings per representative, two 16-bit counts per word
+    union {
+        struct {
+            int16_t rep_uid[LB_MAX];      // unit id of a representative
+            int32_t rep_cnt[LB_MAX / 2];  // strings per representative, two 16-bit counts per word
+        } g;                              // grouping phases
+        Rot<T> hrot[LB_RU];               // unit phase: cos and sin of each unit's current gate
+    } ph;
     uint16_t spid[LB_MAX];      // problem index of each string
-    Rot<T> hrot[LB_RU];         // cos and sin of the current level's gate, per unit
-    Rot<T> srot[MAX_QUBITS];    // cos and sin per qubit (contexts with one problem)
     uint8_t s_idx[LB_MAX];
     int warp_tot[33];
     double drop_sq[LB_WARPS];   // per warp: sum of c^2 dropped (norm tracking only)
@@ -641,9 +659,6 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     const int pass = ctr->pass;
     const long long J = ((long long)offsets[n_fine] + range_target - 1) / range_target;
 
-    const bool batched = run.tab.f64 != nullptr;
-    for (int t = tid; t < MAX_QUBITS; t += LB_THREADS)
-        S.srot[t] = Coef<T>::rot(run, 0u, t);  // one read of the parameter table per qubit
     // per-lane event counts stay far below 2^32 (a launch handles at most
     // 5 entries per string of the capacity, < 2^31, spread over every lane of
     // the grid); the warp totals are summed in 64 bits
@@ -662,7 +677,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         S.n_units = 0;
     }
     for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = 0xffffu;
-    for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.rep_cnt[t] = 0;
+    for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.ph.g.rep_cnt[t] = 0;
     __syncthreads();
     if (S.cur.rj >= J) break;
     if (S.cur.b_next == S.cur.b_lo) {  // one bucket alone exceeds sub_max
@@ -674,16 +689,21 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
 
     // ---- load the range; key of a string = (z, x with the chunk bits cleared)
     for (int i = tid; i < m; i += LB_THREADS) {
-        uint64_t x[W], z[W], f[W], h;
+        uint64_t x[W], z[W], h;
         T c;
         load_record<W, T>(bk, s0 + i, x, z, c, h);
+        int idx;
+        if (pass == 0) {  // from the entry split: full x
+            uint64_t f[W], m[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
-        uint64_t m[W];
-        chunk_mask<W>(f, CHUNK_BITS * pass, m);
-        const int idx = gather_bits<W>(x, m);
+            for (int w = 0; w < W; ++w) f[w] = z[w] & run.mask[w];
+            chunk_mask<W>(f, 0, m);
+            idx = gather_bits<W>(x, m);
 #pragma unroll
-        for (int w = 0; w < W; ++w) x[w] &= ~m[w];
+            for (int w = 0; w < W; ++w) x[w] &= ~m[w];
+        } else {  // from the previous pass: the unit key's x and the slot
+            idx = idx_of(h);
+        }
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             S.sx[w][i] = x[w];
@@ -722,10 +742,10 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         S.s_unit[i] = (int16_t)rep;
         if (rep == i) {  // a new unit: its id, in arbitrary order
             const int u = atomicAdd(&S.n_units, 1);
-            S.rep_uid[i] = (int16_t)u;
+            S.ph.g.rep_uid[i] = (int16_t)u;
             S.u_rep[u] = (int16_t)i;
         }
-        atomicAdd(&S.rep_cnt[rep >> 1], 1 << (16 * (rep & 1)));
+        atomicAdd(&S.ph.g.rep_cnt[rep >> 1], 1 << (16 * (rep & 1)));
     }
     __syncthreads();
     const int n_units = S.n_units;
@@ -739,7 +759,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             v[k] = 0;
             if (u < n_units) {
                 const int r = S.u_rep[u];
-                v[k] = (S.rep_cnt[r >> 1] >> (16 * (r & 1))) & 0xffff;
+                v[k] = (S.ph.g.rep_cnt[r >> 1] >> (16 * (r & 1))) & 0xffff;
             }
             cnt += v[k];
         }
@@ -762,8 +782,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     __syncthreads();
     for (int i = tid; i < m; i += LB_THREADS) {
         const int r = S.s_unit[i];
-        const int u = S.rep_uid[r];
-        const int k = ((atomicSub(&S.rep_cnt[r >> 1], 1 << (16 * (r & 1))) >> (16 * (r & 1))) & 0xffff) - 1;
+        const int u = S.ph.g.rep_uid[r];
+        const int k = ((atomicSub(&S.ph.g.rep_cnt[r >> 1], 1 << (16 * (r & 1))) >> (16 * (r & 1))) & 0xffff) - 1;
         S.s_order[S.ustart[u] + k] = (int16_t)i;
         S.s_unit[i] = (int16_t)u;
         atomicOr(&uocc[u], 1u << S.s_idx[i]);
@@ -786,7 +806,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         uint64_t ppos = 0;  // this pass's chunk positions, 7 bits each (packed_pos)
         int np = 0;
         bool more = false;
-        unsigned upid = 0;
+        unsigned upid = 0, nidx = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) z[w] = xb[w] = xn[w] = 0;
         if (own) {
@@ -803,9 +823,13 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             np = chunk_positions2_packed<W>(f, CHUNK_BITS * pass, ppos, m2, np2);
             more = np2 > 0;
             // the next pass's key: x outside the next chunk (this chunk's bits
-            // are set per output string below; the two chunks are disjoint)
+            // are set per output string below; the two chunks are disjoint),
+            // and the slot in the next unit, the same for all the unit's outputs
+            nidx = (unsigned)gather_bits<W>(xb, m2);
+            // a unit's strings all go on or all end: its outputs' x is the
+            // next pass's key x (next chunk cleared) or the unit key's x
 #pragma unroll
-            for (int w = 0; w < W; ++w) xn[w] = xb[w] & ~m2[w];
+            for (int w = 0; w < W; ++w) xn[w] = more ? xb[w] & ~m2[w] : xb[w];
         }
         if (lane < LB_UPW) S.occ[ub + lane] = own ? uocc[u] : 0u;
         // strings of this warp's units into their slots (a contiguous run of
@@ -834,7 +858,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 dbl = lo & hi;
                 pop_before = __popc(o);
                 qj = packed_pos(ppos, j);
-                S.hrot[ub + lane] = batched ? Coef<T>::rot(run, upid, qj) : S.srot[qj];
+                S.ph.hrot[ub + lane] = Coef<T>::rot(run, upid, qj);
             }
             unsigned tot;
             const unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
@@ -875,10 +899,10 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 const T u1 = S.dense[ur][dcol(ur, y_side ? lb : la)];
                 T na, nb;
                 if (t0 + 32 <= n1) {  // warp-uniform: one-member entries only (2 products)
-                    lone_entry(S.hrot[ur], u1, y_side, na, nb);
+                    lone_entry(S.ph.hrot[ur], u1, y_side, na, nb);
                 } else {
                     const T u2 = two ? S.dense[ur][dcol(ur, lb)] : u1;
-                    pair_entry(S.hrot[ur], u1, u2, two, y_side, na, nb);
+                    pair_entry(S.ph.hrot[ur], u1, u2, two, y_side, na, nb);
                 }
                 const bool ka = keep_t<T>(na, dbits), kb = keep_t<T>(nb, dbits);
                 my_drop += (unsigned)(!ka) + (unsigned)(!kb);
@@ -917,34 +941,41 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
         }
         const unsigned long long base_done = shfl64(bd, 0), base_next = shfl64(bn, 0);
         const unsigned doff = flat - noff;  // done-list offset of this lane's unit
+        // done and next offsets of a lane's unit (each at most LB_UPW * 32 < 2^10)
+        const unsigned dn_off = doff | (noff << 10);
         for (unsigned kb = 0; kb < wtot; kb += 32) {
             const unsigned k = kb + lane;
             // owner lane: last L < LB_UPW with flat(L) <= k
             int lo = 0, hi2 = LB_UPW - 1;
+            unsigned fl = 0;  // flat offset of owner lo (lane 0: 0)
 #pragma unroll
             for (int step = 0; step < LB_UPW_LOG; ++step) {
                 const int mid = (lo + hi2 + 1) >> 1;
                 const unsigned fm = __shfl_sync(FULL_MASK, flat, mid);
-                if (fm <= k)
+                if (fm <= k) {
                     lo = mid;
-                else
+                    fl = fm;
+                } else {
                     hi2 = mid - 1;
+                }
             }
             const int L = lo;
             const unsigned oc = __shfl_sync(FULL_MASK, occ, L);
-            const unsigned fl = __shfl_sync(FULL_MASK, flat, L);
-            const bool mr = __shfl_sync(FULL_MASK, (int)more, L) != 0;
-            const unsigned dof = __shfl_sync(FULL_MASK, doff, L);
-            const unsigned nof = __shfl_sync(FULL_MASK, noff, L);
-            const int npl = __shfl_sync(FULL_MASK, np, L);
+            // problem index, chunk size, next-pass flag and next slot, packed
+            const unsigned pk =
+                __shfl_sync(FULL_MASK, upid | ((unsigned)np << 16) | ((unsigned)more << 19) | (nidx << 20), L);
+            const unsigned ppl = pk & 0xffffu;
+            const int npl = (int)((pk >> 16) & 7u);
+            const bool mr = ((pk >> 19) & 1u) != 0;
+            const unsigned nxi = pk >> 20;
+            const unsigned dno = __shfl_sync(FULL_MASK, dn_off, L);
+            const unsigned dof = dno & 1023u, nof = dno >> 10;
             const uint64_t pp = shfl64(ppos, L);
-            const unsigned ppl = __shfl_sync(FULL_MASK, upid, L);
-            uint64_t x[W], zz[W], x2[W];
+            uint64_t x[W], zz[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                x[w] = shfl64(xb[w], L);
+                x[w] = shfl64(xn[w], L);
                 zz[w] = shfl64(z[w], L);
-                x2[w] = shfl64(xn[w], L);
             }
             if (k >= wtot) continue;
             const int r = (int)(k - fl);
@@ -952,14 +983,12 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
 #pragma unroll
             for (int j = 0; j < CHUNK_BITS; ++j)
                 if (j < npl && ((l >> j) & 1)) {
-                    const int q = packed_pos(pp, j);
-                    set_bit<W>(x, q);
-                    set_bit<W>(x2, q);
+                    set_bit<W>(x, packed_pos(pp, j));
                 }
             const long long slot = (long long)(mr ? base_next + nof + r : base_done + dof + r);
             StrList dst = mr ? next : done;
             uint64_t h = 0;
-            if (mr) h = with_pid(hash_key<W>(zz, x2, ppl), ppl);  // x2: x outside the next chunk
+            if (mr) h = with_idx(with_pid(hash_key<W>(zz, x, ppl), ppl), nxi);  // x: outside the next chunk
             const int rk = mr ? bucket_rank(fcount_next, fine_bucket(h, fshift), ctr) : 0;
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
