@@ -690,6 +690,9 @@ orqa_status build_rx_run(orqa_ctx* ctx, const orqa_gate* g, int ng, double delta
         run.cslf[q] = (float)(run.cs[q] - (double)run.csf[q]);
         run.snlf[q] = (float)(run.sn[q] - (double)run.snf[q]);
     }
+    run.uniform = ctx->P == 1 ? 1 : 0;
+    for (int k = 1; k < ng; ++k)
+        if (g[k].theta != g[0].theta) run.uniform = 0;
     if (ctx->P > 1) {
         const size_t tab = (size_t)ctx->P * MAX_QUBITS;
         std::vector<double2>& h64 = ctx->rot_host[slot];

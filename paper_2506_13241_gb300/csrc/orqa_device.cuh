@@ -109,7 +109,7 @@ struct RxRun {
     uint64_t dbits64;        // threshold as FP64 magnitude bits
     double delta;            // absolute truncation threshold
     int32_t track_norm;      // 1: add c^2 of every string truncation removes to Counters::dropped_sq
-    int32_t pad;
+    int32_t uniform;         // 1: every gate of the run has the same angle (and no per-problem table)
     RotTable tab;            // batched contexts: per-problem angles (else null)
     double cs[MAX_QUBITS];   // cos(theta_q), exact at Clifford angles
     double sn[MAX_QUBITS];   // sin(theta_q)

@@ -65,16 +65,18 @@ __device__ __forceinline__ uint64_t with_idx(uint64_t h, unsigned idx) {
 __device__ __forceinline__ int idx_of(uint64_t h) { return (int)(h >> IDX_SHIFT) & 31; }
 
 // Fine-bucket counts are 16-bit, two per 32-bit word (half the footprint of
-// the randomly addressed count array).  A bucket holds at most sub_max <= 512
-// strings in a valid pass; an increment that finds a count of 2^15 or more
-// raises ERR_BUCKET_OVERFLOW, so no count ever carries into its neighbour
-// unseen (every later kernel returns once the error is set).
-__device__ __forceinline__ int bucket_rank(uint32_t* counts, int b, Counters* ctr) {
-    const int sh = 16 * (b & 1);
-    const int old = (int)((atomicAdd(&counts[b >> 1], 1u << sh) >> sh) & 0xffffu);
-    if (old >= 0x8000) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
-    return old;
+// the randomly addressed count array).  A string takes its rank in its
+// bucket in two steps, so that several increments can be in flight before
+// their results are used: bucket_add returns the word before the increment,
+// bucket_old the string's rank from it.  A bucket holds at most sub_max <=
+// 512 strings in a valid pass; the caller raises ERR_BUCKET_OVERFLOW for a
+// rank of 2^15 or more, so no count ever carries into its neighbour unseen
+// (every later kernel returns once the error is set).
+__device__ __forceinline__ unsigned bucket_add(uint32_t* counts, int b) {
+    return atomicAdd(&counts[b >> 1], 1u << (16 * (b & 1)));
 }
+
+__device__ __forceinline__ int bucket_old(unsigned word, int b) { return (int)((word >> (16 * (b & 1))) & 0xffffu); }
 
 __device__ __forceinline__ int bucket_count(const uint32_t* counts, long long b) {
     return (int)((counts[b >> 1] >> (16 * (b & 1))) & 0xffffu);
@@ -195,12 +197,18 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
         __syncthreads();
         long long sd = (long long)(s_base[0] + (unsigned)(pre & 0xffff));
         long long sa = (long long)(s_base[1] + (unsigned)(pre >> 16));
+        // the tile's routed strings: stores and hashes first, then the
+        // bucket counts of the active ones back to back, so that a thread's
+        // returning atomics overlap
+        long long slot[SPLIT_ITEMS];
+        uint64_t hh[SPLIT_ITEMS];
 #pragma unroll
         for (int k = 0; k < SPLIT_ITEMS; ++k) {
-            if (!kind[k]) continue;
             const long long i = t0 + (long long)k * blockDim.x + threadIdx.x;
             const bool act = kind[k] == 2;
-            const long long slot = act ? sa++ : sd++;
+            slot[k] = act ? sa++ : (kind[k] == 1 ? sd++ : -1);
+            hh[k] = 0;
+            if (!kind[k]) continue;
             StrList dst = act ? active : done;
             const unsigned pid = src.pid ? src.pid[i] : 0u;
             uint64_t x[W];
@@ -210,23 +218,32 @@ __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, Str
             } else {
                 load_plane<W>(src.x, i, x);
             }
-            if (slot < cap) {
-                store_plane<W>(dst.x, slot, x);
-                store_plane<W>(dst.z, slot, z[k]);
-                reinterpret_cast<T*>(dst.c)[slot] = c[k];
-                if (dst.pid) dst.pid[slot] = (uint16_t)pid;
+            if (slot[k] < cap) {
+                store_plane<W>(dst.x, slot[k], x);
+                store_plane<W>(dst.z, slot[k], z[k]);
+                reinterpret_cast<T*>(dst.c)[slot[k]] = c[k];
+                if (dst.pid) dst.pid[slot[k]] = (uint16_t)pid;
             } else {
                 atomicOr(&ctr->err, ERR_OVERFLOW);
             }
-            if (act) {
-                const uint64_t h = unit_hash<W>(x, z[k], run.mask, 0, pid);
-                const int rk = bucket_rank(fcount, fine_bucket(h, fshift), ctr);
-                if (slot < cap) {
-                    active.h[slot] = h;
-                    active.rank[slot] = rk;
+            if (act) hh[k] = unit_hash<W>(x, z[k], run.mask, 0, pid);
+        }
+        unsigned word[SPLIT_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SPLIT_ITEMS; ++k)
+            word[k] = kind[k] == 2 ? bucket_add(fcount, fine_bucket(hh[k], fshift)) : 0u;
+        bool over = false;
+#pragma unroll
+        for (int k = 0; k < SPLIT_ITEMS; ++k)
+            if (kind[k] == 2) {
+                const int rk = bucket_old(word[k], fine_bucket(hh[k], fshift));
+                over = over || rk >= 0x8000;
+                if (slot[k] < cap) {
+                    active.h[slot[k]] = hh[k];
+                    active.rank[slot[k]] = rk;
                 }
             }
-        }
+        if (over) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
         __syncthreads();  // s_base is rewritten by the next tile
     }
     const unsigned long long wd = warp_sum64(my_drop);
@@ -858,7 +875,8 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
                 dbl = lo & hi;
                 pop_before = __popc(o);
                 qj = packed_pos(ppos, j);
-                S.ph.hrot[ub + lane] = Coef<T>::rot(run, upid, qj);
+                // one gate angle for the whole run: a uniform parameter read
+                S.ph.hrot[ub + lane] = run.uniform ? Coef<T>::rot(run, 0u, run.q_first) : Coef<T>::rot(run, upid, qj);
             }
             unsigned tot;
             const unsigned o12 = warp_exclusive_scan((unsigned)__popc(sgl) | ((unsigned)__popc(dbl) << 16), tot);
@@ -988,19 +1006,26 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
             const long long slot = (long long)(mr ? base_next + nof + r : base_done + dof + r);
             StrList dst = mr ? next : done;
             uint64_t h = 0;
-            if (mr) h = with_idx(with_pid(hash_key<W>(zz, x, ppl), ppl), nxi);  // x: outside the next chunk
-            const int rk = mr ? bucket_rank(fcount_next, fine_bucket(h, fshift), ctr) : 0;
+            unsigned word = 0;
+            int b = 0;
+            if (mr) {  // the bucket count is in flight during the stores
+                h = with_idx(with_pid(hash_key<W>(zz, x, ppl), ppl), nxi);  // x: outside the next chunk
+                b = fine_bucket(h, fshift);
+                word = bucket_add(fcount_next, b);
+            }
             if (slot < cap) {
                 store_plane<W>(dst.x, slot, x);
                 store_plane<W>(dst.z, slot, zz);
                 reinterpret_cast<T*>(dst.c)[slot] = S.dense[ub + L][dcol(ub + L, l)];
                 if (dst.pid) dst.pid[slot] = (uint16_t)ppl;
-                if (mr) {
-                    dst.h[slot] = h;
-                    dst.rank[slot] = rk;
-                }
+                if (mr) dst.h[slot] = h;
             } else {
                 atomicOr(&ctr->err, ERR_OVERFLOW);
+            }
+            if (mr) {
+                const int rk = bucket_old(word, b);
+                if (rk >= 0x8000) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
+                if (slot < cap) dst.rank[slot] = rk;
             }
         }
         __syncwarp();
