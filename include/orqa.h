@@ -345,10 +345,11 @@ orqa_status orqa_run_program(orqa_ctx* ctx, const orqa_layer_desc* layers, int32
  *   sub_max        most strings one shared-memory sub-range holds, 128..256;
  *                  the shared hash table has 512 slots, so its load is at
  *                  most sub_max / 512
- *   bucket_density strings per fine bucket at full capacity (8, 16, 32, 64 or
- *                  128, at most sub_max / 4: a bucket must fit one sub-range
- *                  with margin): the number of hash bits that partition the
- *                  strings
+ *   bucket_density most strings per fine bucket on average at full capacity,
+ *                  8..128 and at most sub_max / 3 (a bucket must fit one
+ *                  sub-range with margin; default 80): the bucket count is
+ *                  the power of two at or above capacity / bucket_density,
+ *                  i.e. the number of hash bits that partition the strings
  *   grid_per_sm    CTAs per SM of the streaming kernels, 1..32 */
 typedef struct {
     int32_t range_target;

@@ -68,7 +68,7 @@ struct orqa_ctx {
     uint32_t* fcount = nullptr;     // 16-bit counts, two per word
     int range_target = LB_TARGET;  // strings per unit-kernel range
     int sub_max = LB_MAX;          // most strings of one shared-memory sub-range
-    int bucket_density = 64;       // strings per fine bucket at full capacity
+    int bucket_density = 80;       // strings per fine bucket at full capacity (at most)
     int n_fine_max = 0;            // fine-bucket arrays are sized for this many
     int grid_per_sm = 32;          // CTAs per SM of the streaming kernels
     // captured programs (one per starting buffer) and their device results
@@ -1954,17 +1954,16 @@ orqa_status orqa_get_tuning(orqa_ctx* ctx, orqa_tuning* out) {
 orqa_status orqa_set_tuning(orqa_ctx* ctx, const orqa_tuning* in) {
     if (!ctx || !in) return ORQA_EINVAL;
     if (in->range_target < MIN_RANGE_TARGET || in->range_target > 4096 || in->sub_max < 128 || in->sub_max > LB_MAX ||
-        (in->bucket_density != 8 && in->bucket_density != 16 && in->bucket_density != 32 && in->bucket_density != 64 &&
-         in->bucket_density != 128) ||
+        in->bucket_density < 8 || in->bucket_density > 128 ||
         in->grid_per_sm < 1 ||
         in->grid_per_sm > 32)
         return fail(ctx, ORQA_EINVAL, "set_tuning: value out of range");
-    // a fine bucket holds about bucket_density strings at full capacity and
-    // must fit one shared-memory sub-range; units arrive in clumps of up to
-    // 32 strings, so the bucket-size tail is wider than a Poisson one: keep a
-    // factor 4 of margin
-    if (in->sub_max < 4 * in->bucket_density)
-        return fail(ctx, ORQA_EINVAL, "set_tuning: sub_max must be at least 4 x bucket_density");
+    // a fine bucket holds at most bucket_density strings on average at full
+    // capacity and must fit one shared-memory sub-range; units arrive in
+    // clumps of up to 32 strings, so the bucket-size tail is wider than a
+    // Poisson one: keep a factor 3 of margin
+    if (in->sub_max < 3 * in->bucket_density)
+        return fail(ctx, ORQA_EINVAL, "set_tuning: sub_max must be at least 3 x bucket_density");
     const long long nf = fine_buckets(ctx->cap, in->bucket_density);
     if (nf > ctx->n_fine_max) return fail(ctx, ORQA_EINVAL, "set_tuning: bucket arrays too small");
     ctx->range_target = in->range_target;
@@ -2030,7 +2029,7 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
     if ((st = measure(cur_t, &cur_ms)) != ORQA_OK) return give_up(st);
     const int targets[] = {192, 256, 320, 448, 640};
     const int subs[] = {LB_MAX / 2, LB_MAX};
-    const int densities[] = {16, 32, 64, 128};
+    const int densities[] = {16, 32, 64, 80};
     const int grids[] = {8, 16, 32};
     for (int param = 0; param < 4; ++param) {
         const int* vals = param == 0 ? targets : param == 1 ? subs : param == 2 ? densities : grids;
@@ -2042,7 +2041,7 @@ orqa_status orqa_autotune(orqa_ctx* ctx, const orqa_layer_desc* layers, int32_t 
             if (field == vals[i]) continue;
             field = vals[i];
             if (fine_buckets(ctx->cap, t.bucket_density) > ctx->n_fine_max) continue;
-            if (t.sub_max < 4 * t.bucket_density) continue;
+            if (t.sub_max < 3 * t.bucket_density) continue;
             double ms = 0.0;
             if ((st = measure(t, &ms)) != ORQA_OK) return give_up(st);
             if (ms < cur_ms) {

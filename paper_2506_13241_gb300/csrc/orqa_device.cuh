@@ -300,19 +300,6 @@ __device__ __forceinline__ void set_bit(uint64_t (&v)[W], int q) {
 }
 
 template <int W>
-__device__ __forceinline__ void clear_bit(uint64_t (&v)[W], int q) {
-    if constexpr (W == 1) {
-        v[0] &= ~(1ull << q);
-    } else {
-        const uint64_t b = ~(1ull << (q & 63));
-        if (q < 64)
-            v[0] &= b;
-        else
-            v[1] &= b;
-    }
-}
-
-template <int W>
 __device__ __forceinline__ bool all_zero(const uint64_t (&v)[W]) {
     uint64_t acc = 0;
 #pragma unroll
@@ -393,39 +380,6 @@ __device__ __forceinline__ int nth_set_bit(uint64_t v, int k) {
     }
     if (k >= (int)(w & 1u)) pos += 1;
     return pos;
-}
-
-// Positions (ascending) of the set bits of f whose rank among the set bits
-// is in [skip, skip + CHUNK_BITS); returns how many were found and whether
-// set bits of rank >= skip + CHUNK_BITS remain.
-template <int W>
-__device__ __forceinline__ int chunk_positions(const uint64_t (&f)[W], int skip, int (&pos)[CHUNK_BITS],
-                                               bool& more) {
-    int r = 0;
-    more = false;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        uint64_t v = f[w];
-        if (r == CHUNK_BITS) {
-            more = more || (v != 0);
-            continue;
-        }
-        const int cnt = __popcll(v);
-        if (skip >= cnt) {
-            skip -= cnt;
-            continue;
-        }
-        if (skip > 0) {
-            v &= ~((1ull << nth_set_bit(v, skip)) - 1ull);
-            skip = 0;
-        }
-        while (v != 0 && r < CHUNK_BITS) {
-            pos[r++] = 64 * w + (__ffsll((long long)v) - 1);
-            v &= v - 1;
-        }
-        if (v != 0) more = true;
-    }
-    return r;
 }
 
 // Positions (ascending) of the set bits of f whose rank is in
@@ -538,8 +492,8 @@ __device__ __forceinline__ int gather_bits(const uint64_t (&x)[W], const uint64_
     return idx;
 }
 
-// Hash of a string's unit key for chunk pass `pass` (z, and x with the
-// chunk's bits cleared; see unit_key_hash), from the chunk mask only.
+// Hash of a string's unit key for chunk pass `pass`: z, and x with the
+// chunk's bits cleared (the unit definition of the layer kernels).
 template <int W>
 __device__ __forceinline__ uint64_t unit_hash(const uint64_t (&x)[W], const uint64_t (&z)[W], const uint64_t* mask,
                                               int pass, unsigned pid) {
@@ -549,30 +503,6 @@ __device__ __forceinline__ uint64_t unit_hash(const uint64_t (&x)[W], const uint
     chunk_mask<W>(f, CHUNK_BITS * pass, m);
 #pragma unroll
     for (int w = 0; w < W; ++w) xb[w] = x[w] & ~m[w];
-    return with_pid(hash_key<W>(z, xb, pid), pid);
-}
-
-// Unit key of a string for chunk pass `pass` of an X-rotation run: z and x
-// with the chunk's bits cleared (see the unit definition in the layer
-// kernels).  Returns its 64-bit hash; fills the chunk's qubit positions,
-// their count, the string's packed chunk index and whether F has bits
-// beyond the chunk.
-template <int W>
-__device__ __forceinline__ uint64_t unit_key_hash(const uint64_t (&x)[W], const uint64_t (&z)[W],
-                                                  const uint64_t* mask, int pass, int (&pos)[CHUNK_BITS],
-                                                  int& np, int& idx, bool& more, unsigned pid = 0) {
-    uint64_t f[W], xb[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        f[w] = z[w] & mask[w];
-        xb[w] = x[w];
-    }
-    np = chunk_positions<W>(f, CHUNK_BITS * pass, pos, more);
-    idx = 0;
-    for (int j = 0; j < np; ++j) {
-        idx |= bit_of<W>(x, pos[j]) << j;
-        clear_bit<W>(xb, pos[j]);
-    }
     return with_pid(hash_key<W>(z, xb, pid), pid);
 }
 

@@ -142,6 +142,7 @@ def test_tuning_does_not_change_results(orqa):
     ref = None
     for tune in [dict(), dict(range_target=128, sub_max=256, bucket_density=8, grid_per_sm=1),
                  dict(range_target=1024, sub_max=256, bucket_density=64, grid_per_sm=32),
+                 dict(range_target=448, sub_max=256, bucket_density=85, grid_per_sm=24),
                  dict(range_target=320, sub_max=128, bucket_density=32, grid_per_sm=16)]:
         if tune:
             ctx.set_tuning(**tune)
@@ -153,8 +154,9 @@ def test_tuning_does_not_change_results(orqa):
         else:
             assert_bit_exact(got, ref, str(tune))
             assert np.max(np.abs(m - mref)) < M_TOL
-    for bad in [dict(range_target=64), dict(sub_max=1024), dict(bucket_density=12), dict(grid_per_sm=0),
-                dict(sub_max=128, bucket_density=64)]:  # a bucket must fit a sub-range with a factor 4 of margin
+    for bad in [dict(range_target=64), dict(sub_max=1024), dict(bucket_density=7), dict(bucket_density=129),
+                dict(grid_per_sm=0),
+                dict(sub_max=128, bucket_density=48)]:  # a bucket must fit a sub-range with a factor 3 of margin
         with pytest.raises(orqa.OrqaError) as e:
             ctx.set_tuning(**bad)
         assert e.value.status == orqa.ORQA_EINVAL
