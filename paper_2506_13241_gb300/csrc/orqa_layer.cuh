@@ -128,7 +128,7 @@ __device__ __forceinline__ int block_scan_exclusive(int v, int* warp_tot, int& t
 // own over the operator: it maps each string to one string with |c|
 // unchanged, so the routing below sees exactly the strings that the layer
 // on its own would have left.
-constexpr int SPLIT_ITEMS = 4;
+constexpr int SPLIT_ITEMS = 2;
 
 template <int W, typename T, bool ZZ>
 __global__ void __launch_bounds__(256) k_rx_split(StrList src, StrList done, StrList active, long long cap,
