@@ -360,7 +360,7 @@ def fp64_entry(prof, fp64_ops, sm_mhz):
 # command and figures are in profiles/.  traffic = this ratio x the branch
 # events of an average launch here.  Valid only while the kernel is
 # unchanged: None until it has been measured on the current kernel.
-UNIT_DRAM_BYTES_PER_BRANCH = 27.66
+UNIT_DRAM_BYTES_PER_BRANCH = 27.57
 UNIT_DRAM_SOURCE = "profiles/unit_kernel_traffic_heavyhex_t8_delta3e-5.md"
 
 
