@@ -23,21 +23,28 @@ from paper_2506_13241_gb300 import workloads as W
 CHUNK = 5
 
 
-def _chunk_pass_layer(strings, gates, delta, cos_sin, planted=False):
+def _chunk_pass_layer(strings, gates, delta, cos_sin, planted=False, counts=None):
     """strings: {(x, z): c}; gates: [(q, theta)] on ascending qubits.
     planted: the sin terms of a two-member pair enter with swapped signs
-    (the source-indexed sign of Algorithm 1 as printed)."""
+    (the source-indexed sign of Algorithm 1 as printed).
+    counts (a dict, optional) receives the pieces of the CUDA path's
+    string-gate update count: the strings entering, the strings the entry
+    split drops, and the sum over units and gates of the unit's population
+    change at the gate times the number of the layer's gates above it."""
     M = 0
     rot = {}
     for q, theta in gates:
         M |= 1 << q
         rot[q] = cos_sin(theta)
     q1 = gates[0][0]
+    above = {q: sum(1 for g, _ in gates if g > q) for q, _ in gates}
     kept = lambda v: v != 0.0 and abs(v) >= delta
     done, active = {}, {}
+    split_dropped, upd_w = 0, 0
     for (x, z), c in strings.items():
         f = z & M
         if not (z >> q1) & 1 and not kept(c):
+            split_dropped += 1
             continue                      # truncated after the first gate
         if f == 0:
             done[(x, z)] = c
@@ -76,6 +83,7 @@ def _chunk_pass_layer(strings, gates, delta, cos_sin, planted=False):
                         new[l] = na
                     if kept(nb):
                         new[l | bit] = nb
+                upd_w += (len(new) - len(slots)) * above[q]
                 slots = new
             for l, v in slots.items():
                 x = xb
@@ -85,6 +93,8 @@ def _chunk_pass_layer(strings, gates, delta, cos_sin, planted=False):
                 (nxt if more else done)[(x, z)] = v
         active = nxt
         p += 1
+    if counts is not None:
+        counts.update(n_in=len(strings), split_dropped=split_dropped, upd_w=upd_w)
     return done
 
 
@@ -157,6 +167,37 @@ def test_small_strings_entering_a_layer(oracle_mod):
              ("IZIIII", 1e-5), ("IZIZII", 0.9), ("IYIIZI", -0.3)]
     layer = [("rx", q, None, th) for q, th in ((1, 0.4), (3, -1.1), (4, math.pi / 4))]
     assert _run(oracle_mod, n, terms, [layer, layer], 1e-3) > 4
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_update_count_formula(oracle_mod, seed):
+    """The string-gate update count of an X layer -- the sum over its gates
+    of |O| before the gate, read off the oracle gate by gate -- equals
+    n_g n_in - (strings the entry split drops) (n_g - 1) + the weighted sum
+    of the units' population changes that the unit kernel accumulates."""
+    rng = random.Random(0x13241 + seed)
+    n = rng.choice([8, 12, 20])
+    terms = [("".join(rng.choice("IXYZ") for _ in range(n)), rng.choice([rng.uniform(-1, 1), rng.uniform(-1e-3, 1e-3)]))
+             for _ in range(80)]
+    op = oracle_mod.Oracle(n)
+    for lab, c in terms:
+        op.add_label(lab, c)
+    delta = [0.0, 1e-3][seed % 2]
+    for _ in range(3):
+        qs = sorted(rng.sample(range(n), rng.randint(2, n)))
+        layer = [("rx", q, None, rng.choice([0.3, -0.8, math.pi / 4, 1.3])) for q in qs]
+        before = _as_planes(oracle_mod, op, n)
+        expected = 0
+        for g in layer:
+            expected += len(op)
+            op.apply(g, delta)
+        counts = {}
+        got = _chunk_pass_layer(before, [(g[1], g[3]) for g in layer], delta, oracle_mod.rotation_cos_sin,
+                                counts=counts)
+        assert got == _as_planes(oracle_mod, op, n)
+        ng = len(layer)
+        formula = ng * counts["n_in"] - counts["split_dropped"] * (ng - 1) + counts["upd_w"]
+        assert formula == expected, (formula, expected, counts)
 
 
 def test_planted_sign_is_caught(oracle_mod):
