@@ -689,20 +689,23 @@ __global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
     if (wp == LB_WARPS - 1) next_subrange(S, ctr, range_start, offsets, J, sub_max, true, bk, record_bytes(W));
     for (;;) {  // block-uniform
     __syncthreads();  // the prepared item is visible; the previous one is finished
+    // every thread reads the prepared item (warp LB_WARPS - 1 rewrites it
+    // only in the unit phase, after the barriers below), so the table
+    // clearing and the load share one phase
+    const SubRange cur = S.nx;
     if (tid == 0) {
-        S.cur = S.nx;
+        S.cur = cur;
         S.n_units = 0;
     }
-    for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = 0xffffu;
-    for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.ph.g.rep_cnt[t] = 0;
-    __syncthreads();
-    if (S.cur.rj >= J) break;
-    if (S.cur.b_next == S.cur.b_lo) {  // one bucket alone exceeds sub_max
+    if (cur.rj >= J) break;
+    if (cur.b_next == cur.b_lo) {  // one bucket alone exceeds sub_max
         if (tid == 0) atomicOr(&ctr->err, ERR_BUCKET_OVERFLOW);
         break;
     }
-    const long long s0 = S.cur.s0;
-    const int m = (int)(S.cur.s1 - S.cur.s0);
+    for (int t = tid; t < LB_TABLE; t += LB_THREADS) S.table[t] = 0xffffu;
+    for (int t = tid; t < LB_MAX / 2; t += LB_THREADS) S.ph.g.rep_cnt[t] = 0;
+    const long long s0 = cur.s0;
+    const int m = (int)(cur.s1 - cur.s0);
 
     // ---- load the range; key of a string = (z, x with the chunk bits cleared)
     for (int i = tid; i < m; i += LB_THREADS) {
