@@ -29,11 +29,12 @@
 
 namespace orqa {
 
-// Four warps per CTA and six CTAs per SM (shared memory: about 37 KB per
-// CTA): with the sub-range barriers of small CTAs the warps wait less for
-// the slowest one than with 8-warp CTAs (measured: 3-4% faster unit kernel
-// at the 1e9-string heavy-hex workload than 8 warps x 3 CTAs, and faster
-// than 32 units per warp).
+// Four warps per CTA and seven CTAs per SM (shared memory: 32,000 B per
+// CTA at W = 2 in FP64; 7 x 128 threads leave 73 registers a thread): with
+// the sub-range barriers of small CTAs the warps wait less for the slowest
+// one than with 8-warp CTAs (measured at the 1e9-string heavy-hex workload:
+// 4-warp CTAs x 6 were 3-4% faster than 8 warps x 3 and faster than 32
+// units per warp; 7 per SM are 5% faster than 6).
 constexpr int LB_THREADS = 128;
 constexpr int LB_CTAS_PER_SM = 7;  // resident unit-kernel CTAs per SM (launch bound)
 constexpr int LB_WARPS = LB_THREADS / 32;
