@@ -70,7 +70,7 @@ def test_batch_matches_oracle(orqa, oracle_mod, steps, weights, n_theta):
 
 
 def test_batch_equals_plain_contexts(orqa):
-    """The cfg-5 problem mix at reduced size (8 angles x weights 1, 3, 17,
+    """The theta x observable sweep's problem mix at reduced size (8 angles x weights 1, 3, 17,
     2 steps, delta = 1e-3): every problem of the batch equals the same
     problem run alone in a plain context."""
     wl = W.sweep_workload(8, 2, 1e-3)

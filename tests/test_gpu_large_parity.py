@@ -1,5 +1,5 @@
-"""Element-by-element parity at more than 1e7 strings: heavy-hex (BASELINE
-config 2's circuit: theta = pi/4, Z_62) for 6 steps at delta = 2e-5, where
+"""Element-by-element parity at more than 1e7 strings: the 127-qubit
+heavy-hex kicked Ising circuit (theta = pi/4, Z_62) for 6 steps at delta = 2e-5, where
 the operator holds 12,716,456 strings.  The single-threaded oracle needs
 minutes for this, so the oracle runs sharded by owner(z) over CPU gloo ranks
 (one oracle per rank; the sharding is exact, see test_shard_ranks.py, which

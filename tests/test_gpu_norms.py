@@ -59,7 +59,7 @@ def test_norms_match_oracle_and_balance_per_layer(orqa, oracle_mod):
 
 
 def test_norm_conserved_without_truncation(orqa):
-    """12-qubit chain at delta = 0 (BASELINE config 1): sum c^2 stays 1 and
+    """12-qubit chain, theta = pi/4, Z_6, 5 steps at delta = 0: sum c^2 stays 1 and
     nothing is dropped."""
     wl = W.workload("chain12")
     ctx = orqa.Context(wl["n"], 1 << 20)

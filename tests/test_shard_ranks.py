@@ -86,8 +86,8 @@ def _check_against_oracle(parts, oracle_mod, steps, delta):
 
 @pytest.mark.slow
 def test_two_ranks_match_single_oracle(tmp_path, oracle_mod):
-    """BASELINE config 2 (heavy-hex, theta = pi/4, Z_62, 5 steps, delta =
-    1e-4) sharded over two gloo ranks."""
+    """The 127-qubit heavy-hex kicked Ising circuit (theta = pi/4, Z_62, 5
+    steps, delta = 1e-4) sharded over two gloo ranks."""
     parts = _run(2, tmp_path, 5, 1e-4)
     _check_against_oracle(parts, oracle_mod, 5, 1e-4)
     assert all(int(p["exchanged"]) > 0 for p in parts)  # the ZZ layers did move strings
