@@ -362,6 +362,11 @@ def fp64_entry(prof, fp64_ops, sm_mhz):
 # unchanged: None until it has been measured on the current kernel.
 UNIT_DRAM_BYTES_PER_BRANCH = 27.57
 UNIT_DRAM_SOURCE = "profiles/unit_kernel_traffic_heavyhex_t8_delta3e-5.md"
+# What bounds the unit kernel, from its ncu full capture (fractions of each
+# unit's peak on the few-GB heavy-hex case; the same validity rule): issue
+# slots and the ALU and FP64 pipes are busy, DRAM is not.
+UNIT_LIMITER = {"issue_active": 0.672, "alu_pipe": 0.657, "fp64_pipe": 0.558, "dram_throughput": 0.086,
+                "warps_active": 0.434, "source": "profiles/unit_kernel_heavyhex_t8_delta3e-5.md"}
 
 
 def roofline_entry(prof, steps, workload=None, precision="fp64", n_qubits=127):
@@ -400,6 +405,8 @@ def roofline_entry(prof, steps, workload=None, precision="fp64", n_qubits=127):
         branches_per_launch = floor_b / per_branch / dom["launches"]
         entry["traffic"] = UNIT_DRAM_BYTES_PER_BRANCH * branches_per_launch
         entry["traffic_source"] = UNIT_DRAM_SOURCE + " (DRAM bytes per branch event x branch events per launch)"
+        if precision == "fp64" and UNIT_LIMITER:
+            entry["limiter"] = dict(UNIT_LIMITER)
     return entry
 
 

@@ -38,8 +38,10 @@ def test_roofline_entry_uses_the_dominant_kernel():
         bench.UNIT_DRAM_BYTES_PER_BRANCH = None
         assert bench.roofline_entry(prof, 1)["traffic"] is None
         bench.UNIT_DRAM_BYTES_PER_BRANCH = 100.0
-        t = bench.roofline_entry(prof, 1)["traffic"]
-        assert abs(t - 100.0 * 1e8 / 4) < 1e-3                    # 2.5e7 branch events per launch
+        r = bench.roofline_entry(prof, 1)
+        assert abs(r["traffic"] - 100.0 * 1e8 / 4) < 1e-3          # 2.5e7 branch events per launch
+        # the captured limiter of the unit kernel rides along, with its source
+        assert r["limiter"]["source"].startswith("profiles/") and 0 < r["limiter"]["issue_active"] <= 1
     finally:
         bench.UNIT_DRAM_BYTES_PER_BRANCH = old
 
