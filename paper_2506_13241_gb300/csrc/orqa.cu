@@ -745,7 +745,7 @@ RxLists rx_lists(orqa_ctx* ctx, int S) {
 
 int local_grid(const orqa_ctx* ctx, long long n_active) {
     const long long ranges = (n_active + ctx->range_target - 1) / ctx->range_target;
-    const long long cap = (long long)ctx->sm_count * LB_CTAS_PER_SM;  // resident CTAs of the unit kernel
+    const long long cap = (long long)ctx->sm_count * (ctx->fp32 ? lb_ctas<float>() : lb_ctas<double>());  // resident CTAs of the unit kernel
     return (int)std::max(1ll, std::min(ranges, cap));
 }
 
@@ -1736,7 +1736,7 @@ orqa_status capture_program(orqa_ctx* ctx, const std::vector<ProgLayer>& pl, int
     int cur = ctx->cur;
     size_t off = 0;
     const int g_stream = ctx->sm_count * ctx->grid_per_sm;
-    const int g_local = ctx->sm_count * LB_CTAS_PER_SM;
+    const int g_local = ctx->sm_count * lb_ctas<T>();
     cudaGraph_t graph = nullptr;
     const ZZGroups* held = nullptr;  // a ZZ layer left to the next entry split
     ctx->profile = false;

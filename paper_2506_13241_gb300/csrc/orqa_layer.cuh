@@ -34,9 +34,13 @@ namespace orqa {
 // the sub-range barriers of small CTAs the warps wait less for the slowest
 // one than with 8-warp CTAs (measured at the 1e9-string heavy-hex workload:
 // 4-warp CTAs x 6 were 3-4% faster than 8 warps x 3 and faster than 32
-// units per warp; 7 per SM are 5% faster than 6).
+// units per warp; 7 per SM are 5% faster than 6).  FP32 coefficients need
+// 22,776 B and 64 registers, so 8 CTAs fit (3% faster than 7).
 constexpr int LB_THREADS = 128;
-constexpr int LB_CTAS_PER_SM = 7;  // resident unit-kernel CTAs per SM (launch bound)
+constexpr int LB_CTAS_PER_SM = 7;  // resident unit-kernel CTAs per SM (launch bound), FP64
+// FP32 coefficients: smaller shared-memory rows leave room for one more CTA
+template <typename T>
+constexpr int lb_ctas() { return sizeof(T) == 4 ? 8 : LB_CTAS_PER_SM; }
 constexpr int LB_WARPS = LB_THREADS / 32;
 constexpr int LB_MAX = 256;         // most strings one CTA sub-range may hold
 constexpr int LB_TARGET = 448;      // strings per CTA range, on average (default tuning)
@@ -665,7 +669,7 @@ __device__ __forceinline__ void next_subrange(Smem& S, Counters* ctr, const int3
 // most sub_max / LB_TABLE).  TRACK adds up the c^2 of the dropped strings
 // (the norm bookkeeping); the timed path is compiled without it.
 template <int W, typename T, bool TRACK>
-__global__ void __launch_bounds__(LB_THREADS, LB_CTAS_PER_SM) k_bucket_local(
+__global__ void __launch_bounds__(LB_THREADS, lb_ctas<T>()) k_bucket_local(
     const void* bk, const uint32_t* __restrict__ offsets, const int32_t* __restrict__ range_start,
     long long n_fine, int range_target, int sub_max, const __grid_constant__ RxRun run, StrList done,
     StrList next, long long cap, Counters* ctr, uint32_t* fcount_next, int fshift) {
