@@ -153,3 +153,20 @@ def test_noalloc_rejects_bad_sizes_before_any_cuda_call(lib):
     assert lib.orqa_expect_noalloc(127, orqa.ORQA_NOALLOC_MAX_STRINGS + 1, None, None, ctypes.byref(d),
                                    None) == orqa.ORQA_ECAPACITY
     assert lib.orqa_expect_noalloc(127, 5, None, None, ctypes.byref(d), None) == orqa.ORQA_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """Every ORQA_* constant the header defines (enum members with explicit
+    values and #define'd numbers) has the same value in the binding, so the
+    binding stays thin marshalling of the C declarations."""
+    header = open(HEADER).read()
+    header = re.sub(r"/\*.*?\*/", " ", header, flags=re.S)
+    found = {}
+    for name, value in re.findall(r"\b(ORQA_[A-Z0-9_]+)\s*=\s*(\d+)", header):
+        found[name] = int(value)
+    for name, value in re.findall(r"#define\s+(ORQA_[A-Z0-9_]+)\s+(\d+)(?:LL)?\b", header):
+        found[name] = int(value)
+    assert len(found) >= 20
+    for name, value in sorted(found.items()):
+        assert hasattr(orqa, name), name
+        assert getattr(orqa, name) == value, (name, getattr(orqa, name), value)
